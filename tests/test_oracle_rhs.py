@@ -1,0 +1,280 @@
+"""Pins of the oracle's right-hand side (Eqs. 1, 4, 5): exact balances,
+free-stream and linear-field exactness on curved meshes, discrete
+conservation, closed forms, symmetries, and convergence to the analytic
+divergence of a manufactured state."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1511_01561_gb300 import inputs as I
+
+
+def _gamma(cfg):
+    return cfg["cp"] / cfg["cv"]
+
+
+# ---------------------------------------------------------------- EOS ----
+
+def test_eos_zero_and_naive_agreement(orc):
+    cfg = I.box(1, 1)
+    gam = _gamma(cfg)
+    th0, p0 = 348.0, 1.0e5
+    p_ref = cfg["P00"] * (cfg["Rd"] * th0 / cfg["P00"]) ** gam
+    assert orc.pprime(0.0, th0, p_ref, gam) == 0.0
+    for x in (1e-4, -3e-3, 2e-2, -0.1, 0.3):
+        a = orc.pprime(x * th0, th0, p_ref, gam)
+        b = orc.pprime_naive(x * th0, th0, p_ref, cfg)
+        assert abs(a - b) <= 1e-10 * abs(a)
+        # (1+x)^gamma - 1 by the binomial series, independent of libm
+        s, term = 0.0, 1.0
+        for k in range(1, 60):
+            term *= (gam - k + 1) / k * x
+            s += term
+        assert abs(a - p_ref * s) <= 2e-15 * abs(a)
+    # tiny perturbations keep full relative accuracy (first-order term)
+    x = 1e-12
+    a = orc.pprime(x * th0, th0, p0, gam)
+    assert abs(a / (p0 * gam * x) - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("ref", ["isentropic", "isothermal"])
+def test_reference_state_is_hydrostatic(orc, ref):
+    """dp0/dz = -rho0 g and p0 = p(rho theta_0) on a fine column."""
+    cfg = I.box((1, 1, 16), 4, L=(100.0, 100.0, 10000.0), ref=ref, T0=250.0)
+    m = orc.Mesh(cfg)
+    xyz, (rho0, th0, p0) = m.coords(), m.ref()
+    col = (np.abs(xyz[0]) < 1e-9) & (np.abs(xyz[1]) < 1e-9)
+    z, p, r = xyz[2][col], p0[col], rho0[col]
+    o = np.argsort(z)
+    z, p, r = z[o], p[o], r[o]
+    c = np.polynomial.polynomial.polyfit(z / 1e4, p / 1e5, 14)
+    dpdz = np.polynomial.polynomial.polyval(z / 1e4, np.polynomial.polynomial.polyder(c)) * 1e5 / 1e4
+    np.testing.assert_allclose(dpdz, -r * cfg["g"], rtol=1e-7)
+    gam = _gamma(cfg)
+    peos = cfg["P00"] * (cfg["Rd"] * th0 / cfg["P00"]) ** gam
+    np.testing.assert_allclose(peos, p0, rtol=1e-13)
+
+
+# ------------------------------------------------------- exact balances ----
+
+@pytest.mark.parametrize(
+    "cfg",
+    [I.box(3, 4), I.box(2, 3, ref="isothermal", T0=250.0), I.box(2, 4, warp=0.05), I.shell(2, 2, 3)],
+)
+def test_rest_state_gives_zero_rhs_bitwise(orc, cfg):
+    m = orc.Mesh(cfg)
+    R = m.rhs(m.init_state("rest"))
+    assert np.all(R == 0.0)
+
+
+@pytest.mark.parametrize("warp", [0.0, 0.05])
+def test_uniform_flow_without_gravity_is_preserved(orc, warp):
+    cfg = I.box((3, 2, 2), 4, periodic=(1, 1, 1), warp=warp, g=0.0)
+    m = orc.Mesh(cfg)
+    q = m.init_state("uniform", (10.0, -4.0, 2.5))
+    R = m.rhs(q)
+    rho0 = m.ref()[0].max()
+    scale = rho0 * 10.0 * 10.0 / (1000.0 / 12)  # rho |u|^2 / dx_min
+    assert np.abs(R).max() < 1e-12 * scale
+
+
+def test_linear_pressure_gradient_exact_on_curved_meshes(orc):
+    """With U = 0 and p' linear in x, R_U = -grad p' exactly at non-wall
+    nodes on any isoparametric mesh: the isoparametric metrics invert the
+    coordinate derivatives exactly.  Transposing D or the metric fails this."""
+    b = np.array([3.0e-3, -2.0e-3, 5.0e-3])
+    for cfg in (I.box((2, 3, 2), 4, warp=0.06, g=0.0), I.shell(2, 2, 4, g=0.0, Omega=0.0)):
+        m = orc.Mesh(cfg)
+        xyz = m.coords()
+        rho0, th0, p0 = m.ref()
+        pp = (b @ (xyz - xyz.mean(axis=1, keepdims=True))) * (1.0 if cfg["kind"] == "shell" else 1e3)
+        gam = _gamma(cfg)
+        q = np.zeros((5, m.Ng))
+        q[4] = th0 * ((1.0 + pp / p0) ** (1.0 / gam) - 1.0)
+        R = m.rhs(q)
+        bb = b * (1.0 if cfg["kind"] == "shell" else 1e3)
+        wall = m.wall()
+        inner = wall == 0
+        for a in range(3):
+            assert np.abs(R[1 + a][inner] + bb[a]).max() < 1e-9 * np.abs(bb).max(), a
+        assert np.abs(R[0]).max() == 0.0 and np.abs(R[4]).max() == 0.0
+
+
+def test_linear_momentum_divergence_exact(orc):
+    G = np.array([[0.3, -0.7, 0.2], [0.5, 0.1, -0.4], [-0.6, 0.9, 0.25]]) * 1e-2
+    cfg = I.box((2, 2, 3), 4, warp=0.05, g=0.0)
+    m = orc.Mesh(cfg)
+    xyz = m.coords()
+    q = np.zeros((5, m.Ng))
+    q[1:4] = G @ xyz
+    R = m.rhs(q)
+    assert np.abs(R[0] + np.trace(G)).max() < 1e-12 * 1e3 * np.abs(G).max()
+
+
+# --------------------------------------------------------- conservation ----
+
+@pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1)])
+def test_discrete_conservation(orc, periodic):
+    g = 9.81 if not any(periodic) else 0.0
+    cfg = I.box((3, 2, 2), 4, periodic=periodic, g=g)
+    m = orc.Mesh(cfg)
+    q = I.random_perturbation(m.Ng, seed=3)
+    wall = m.wall()
+    for a in range(3):
+        q[1 + a][(wall >> a) & 1 == 1] = 0.0
+    R = m.rhs(q)
+    M = m.mass()
+    vars_ = [0, 4] if not any(periodic) else [0, 1, 2, 3, 4]
+    for v in vars_:
+        tot = M @ R[v]
+        assert abs(tot) < 1e-13 * (M @ np.abs(R[v])), v
+
+
+# ------------------------------------------------------------ closed form ----
+
+def test_bubble_first_rhs_closed_form(orc):
+    cfg = I.box(4, 4)
+    m = orc.Mesh(cfg)
+    q = m.init_state("bubble", I.BUBBLE_PARAMS)
+    assert np.all(q[1:] == 0.0) and q[0].min() < 0.0
+    R = m.rhs(q)
+    assert np.all(R[[0, 1, 2, 4]] == 0.0)
+    wall = m.wall()
+    top_bottom = (wall & 4) != 0
+    assert np.all(R[3][top_bottom] == 0.0)
+    exact = -q[0] * cfg["g"]
+    np.testing.assert_allclose(R[3][~top_bottom], exact[~top_bottom], rtol=1e-14, atol=0)
+
+
+def test_bubble_initial_state(orc):
+    cfg = I.box(4, 4)
+    m = orc.Mesh(cfg)
+    q = m.init_state("bubble", I.BUBBLE_PARAMS)
+    xyz = m.coords()
+    rho0, th0, _ = m.ref()
+    r = np.sqrt(((xyz - np.array([[500.0], [500.0], [350.0]])) ** 2).sum(axis=0))
+    thp = np.where(r <= 250.0, 0.25 * (1 + np.cos(np.pi * r / 250.0)), 0.0)
+    theta = th0 / (rho0 + q[0])
+    np.testing.assert_allclose(theta - 300.0, thp, atol=1e-11)
+
+
+# ------------------------------------------------------------- symmetry ----
+
+def _box_grid(m, cfg):
+    nx = [cfg["ne"][a] * cfg["N"] + 1 for a in range(3)]
+    return nx
+
+
+def test_mirror_and_swap_symmetry(orc):
+    cfg = I.box((3, 3, 2), 4)
+    m = orc.Mesh(cfg)
+    nx, ny, nz = _box_grid(m, cfg)
+    xyz = m.coords()
+    q = I.smooth_perturbation(xyz, seed=11, length=700.0)
+
+    def grid(a):
+        return a.reshape(5, nz, ny, nx)
+
+    Q = grid(q.copy())
+    # x- and y-mirror symmetric state: U_x odd in x, U_y odd in y
+    Qm = Q[:, :, :, ::-1].copy()
+    Qm[1] *= -1
+    Q = 0.5 * (Q + Qm)
+    Qm = Q[:, :, ::-1, :].copy()
+    Qm[2] *= -1
+    Q = 0.5 * (Q + Qm)
+    # x<->y swap symmetric state (keeps both mirror symmetries)
+    Qs = Q.transpose(0, 1, 3, 2).copy()
+    Qs[[1, 2]] = Qs[[2, 1]]
+    Q = 0.5 * (Q + Qs)
+    q = Q.reshape(5, -1)
+    R = grid(m.rhs(q))
+    scale = np.abs(R).max(axis=(1, 2, 3))
+    Rm = R[:, :, :, ::-1].copy()
+    Rm[1] *= -1
+    for v in range(5):
+        assert np.abs(R[v] - Rm[v]).max() <= 1e-12 * scale[v], v
+    Rs = R.transpose(0, 1, 3, 2).copy()
+    Rs[[1, 2]] = Rs[[2, 1]]
+    for v in range(5):
+        assert np.abs(R[v] - Rs[v]).max() <= 1e-12 * scale[v], v
+
+
+# ------------------------------------------------------- manufactured ----
+
+def _manufactured(cfg):
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    Lx, Ly, Lz = cfg["L"]
+    X, Y, Zs = x / Lx, y / Ly, z / Lz
+    Rd, cp, cv, P00, g, th0 = (cfg[k] for k in ("Rd", "cp", "cv", "P00", "g", "theta0"))
+    gam = sp.Rational(cp * 2, 1) / sp.Rational(cv * 2, 1)
+    pi0 = 1 - g * z / (cp * th0)
+    p0 = P00 * pi0 ** (cp / Rd)
+    Th0 = p0 / (Rd * pi0)
+    rho0 = Th0 / th0
+    rp = 0.01 * sp.sin(2 * sp.pi * X + 0.3) * sp.cos(sp.pi * Y) * sp.cos(sp.pi * Zs + 0.2)
+    U = [3.0 * sp.sin(sp.pi * X + 0.4) * sp.cos(2 * sp.pi * Y + 0.1) * sp.cos(sp.pi * Zs),
+         2.0 * sp.cos(sp.pi * X + 0.2) * sp.sin(sp.pi * Y + 0.5) * sp.cos(sp.pi * Zs + 0.3),
+         1.5 * sp.cos(sp.pi * X) * sp.cos(sp.pi * Y + 0.3) * sp.sin(sp.pi * Zs + 0.6)]
+    Tp = 0.5 * sp.cos(sp.pi * X) * sp.cos(sp.pi * Y + 0.4) * sp.sin(2 * sp.pi * Zs + 0.5)
+    rho = rho0 + rp
+    theta = (Th0 + Tp) / rho
+    pp = P00 * (Rd * (Th0 + Tp) / P00) ** gam - p0
+    u = [Ui / rho for Ui in U]
+    xs = (x, y, z)
+    Rr = -sum(sp.diff(U[c], xs[c]) for c in range(3))
+    RU = [-sum(sp.diff(U[a] * u[c] + (pp if a == c else 0), xs[c]) for c in range(3)) for a in range(3)]
+    RU[2] += -rp * g
+    RT = -sum(sp.diff(theta * U[c], xs[c]) for c in range(3))
+    fields = [rp, U[0], U[1], U[2], Tp]
+    rhs = [Rr, RU[0], RU[1], RU[2], RT]
+    f_state = sp.lambdify((x, y, z), fields, "numpy")
+    f_rhs = sp.lambdify((x, y, z), rhs, "numpy")
+    return f_state, f_rhs
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_manufactured_state_converges_to_analytic_rhs(orc, N):
+    """On a warped box the discrete R converges to -div F + S of a smooth
+    analytic state at the rate of the order-N interpolant (Eqs. 4-5)."""
+    errs = []
+    for ne in (4, 8):
+        cfg = I.box(ne, N, L=(1000.0, 800.0, 600.0), warp=0.04)
+        m = orc.Mesh(cfg)
+        f_state, f_rhs = _manufactured(cfg)
+        xyz = m.coords()
+        q = np.array([np.broadcast_to(f, xyz[0].shape) for f in f_state(*xyz)])
+        ex = np.array([np.broadcast_to(f, xyz[0].shape) for f in f_rhs(*xyz)])
+        R = m.rhs(q)
+        inner = m.wall() == 0
+        e = [np.abs(R[v][inner] - ex[v][inner]).max() / np.abs(ex[v]).max() for v in range(5)]
+        errs.append(e)
+    errs = np.array(errs)
+    assert np.all(errs[-1] < 3e-3), errs
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(rates > N - 1.2), (errs, rates)
+
+
+def test_isothermal_rest_about_isentropic_reference_converges(orc):
+    """An isothermal atmosphere at rest written as a perturbation of the
+    isentropic reference is in hydrostatic balance only up to the
+    discretisation error, which must fall quickly with the order."""
+    errs = []
+    for N in (2, 4, 6):
+        cfg = I.box((1, 1, 4), N, L=(1000.0, 1000.0, 8000.0))
+        m = orc.Mesh(cfg)
+        rho0, th0, p0 = m.ref()
+        z = m.coords()[2]
+        T0, Rd, P00, cp, cv, g = 260.0, cfg["Rd"], cfg["P00"], cfg["cp"], cfg["cv"], cfg["g"]
+        piso = P00 * np.exp(-g * z / (Rd * T0))
+        rho_iso = piso / (Rd * T0)
+        th_iso = (P00 / Rd) * (piso / P00) ** (cv / cp)
+        q = np.zeros((5, m.Ng))
+        q[0] = rho_iso - rho0
+        q[4] = th_iso - th0
+        R = m.rhs(q)
+        inner = m.wall() == 0
+        errs.append(np.abs(R[3][inner]).max() / (g * np.abs(q[0]).max()))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10, errs
