@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the CG spectral-element RHS / SSP-RK3 hot path (NUMA, Sec. 2).
+
+Workload (default): the rising thermal bubble in a 1000 m box with 32^3
+elements of order N=4 (129^3 = 2,146,689 global nodes), FP64, dt = 0.01 s.
+One benchmark step is one SSP-RK3 time step = three RK stages, each
+create_rhs (element volume kernel) + DSS / inverse mass / update kernel.
+Metric: node-updates per second per RK stage = Ng * 3 * steps / time.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (each step: one full SSP-RK3 step of the same
+workload).  With torchrun (N > 1) every rank advances its own replica of the
+workload on its own GPU (no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "node-updates/s per RK stage"
+UNIT = "node-updates/s"
+STAGES = 3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    p.add_argument("--workload", default="bubble_32x32x32_N4")
+    p.add_argument("--no-fp32", action="store_true", help="skip the FP32 mixed-precision line")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 peak of the GB300 (dense, non-tensor): the nominal 1.25 TFLOP/s of the
+# profiling recipe; a register-only DFMA probe on this pool measured 1.19.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def volume_flops_per_elem_node(N: int) -> float:
+    """Algorithmic FP64 flops per element node of create_rhs: 39 contractions
+    of length N+1 (2 flops each) plus about 150 pointwise flops."""
+    return 78.0 * (N + 1) + 150.0
+
+
+def volume_bytes(Nl: int, Ng: int, met_bytes: int) -> float:
+    """Algorithmic DRAM bytes of one volume-kernel launch: metric terms and
+    Jw (10 per element node), l2g (4 B), r_e write (5 FP64), and one read of
+    the gathered state and reference (8 FP64 per global node)."""
+    return Nl * (10 * met_bytes + 4 + 40) + Ng * 64
+
+
+def update_bytes(Nl: int, Ng: int, stage_reads_qn: float) -> float:
+    """Algorithmic DRAM bytes of one DSS/update launch: CSR (4 B per entry +
+    4 B per node), r_e read (5 FP64 per element node), M^-1, wall flag, q^k
+    read, q^{k+1} write, and q^n on the stages that use it."""
+    return Nl * (4 + 40) + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn)
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_worker(args):
+    """Time the FP64 CPU oracle on the host cores (child process)."""
+    from oracle import oracle
+    from paper_1511_01561_gb300 import inputs as I
+
+    w = I.WORKLOADS[args.workload]
+    m = oracle.Mesh(w["cfg"])
+    q = m.init_state(*w["ic"])
+    t0 = time.perf_counter()
+    q = m.run(q, w["dt"], 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(round(args.cpu_seconds / max(t1, 1e-3))) - 1)
+    t0 = time.perf_counter()
+    m.run(q, w["dt"], n)
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    print(json.dumps({"value": m.Ng * STAGES * n / t, "steps": n, "seconds": t, "cores": cores,
+                      "Ng": m.Ng}))
+
+
+def cpu_baseline(args):
+    env = dict(os.environ)
+    env.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", args.workload,
+                        "--cpu-seconds", str(args.cpu_seconds)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": f"{d['steps']} SSP-RK3 steps ({STAGES * d['steps']} stages) of {args.workload} "
+                      f"on all {d['Ng']} global nodes, {d['seconds']:.1f} s, FP64 C oracle (-O2, OpenMP)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, each step one SSP-RK3 step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1511_01561_gb300 import inputs as I
+
+    w = I.WORKLOADS[args.workload]
+    m = oracle.Mesh(w["cfg"])
+    q = m.init_state(*w["ic"])
+    if args.warmup:
+        q = m.run(q, w["dt"], args.warmup)
+    t0 = time.perf_counter()
+    m.run(q, w["dt"], args.steps)
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = m.Ng * STAGES * args.steps / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "global_nodes": m.Ng, "elements": m.Ne, "N": w["cfg"]["N"],
+                   "dt": w["dt"], "rk": "ssp-rk3"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} SSP-RK3 steps of {args.workload}, all global nodes"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_mine(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)  # child process, before heavy GPU work
+
+    from paper_1511_01561_gb300 import inputs as I
+    from paper_1511_01561_gb300 import numa
+
+    w = I.WORKLOADS[args.workload]
+    cfg, dt = w["cfg"], w["dt"]
+    hbm_gbs, peak_src = load_peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def measure(precision):
+        s = numa.Solver(cfg, precision, device=str(dev))
+        s.init_state(*w["ic"])
+        s.run(dt, args.warmup)
+        stream = s.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local) if precision == "fp64" else None
+        e0.record(stream)
+        s.run(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        ck = clocks.stop() if clocks else None
+        # per-kernel device times over the same number of steps (event-bracketed launches)
+        ms_vol, ms_upd = s.time_kernels(dt, args.steps)
+        info = s.info
+        e2e = None
+        if not args.no_e2e and precision == "fp64":
+            q_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
+            out_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
+            s.get_state(q_host)
+            nb = 5 * s.Ng * 8
+            barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                numa.numa_set_state(s.ctx, q_host.data_ptr(), False)
+                numa.numa_rk_step(s.ctx, dt)
+                numa.numa_get_state(s.ctx, out_host.data_ptr(), False)
+            torch.cuda.synchronize(dev)
+            te = max_over_ranks(time.perf_counter() - t0)
+            e2e = {"value": world * s.Ng * STAGES * args.steps / te, "unit": UNIT,
+                   "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        finite = s.check_finite() == 0
+        s.close()
+        return ms, ms_vol, ms_upd, info, e2e, ck, finite
+
+    ms, ms_vol, ms_upd, info, e2e, ck, finite = measure("fp64")
+    Ng, Nl, N = info["Ng"], info["Nl"], info["N"]
+    value = world * Ng * STAGES * args.steps / (ms * 1e-3)
+    nlaunch = STAGES * args.steps
+    vol_avg_s = ms_vol * 1e-3 / nlaunch
+    flops = volume_flops_per_elem_node(N) * Nl
+    achieved_tf = flops / vol_avg_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "global_nodes": Ng, "elements": info["Ne"], "N": N, "dt": dt,
+                   "rk": "ssp-rk3", "stages_per_step": STAGES,
+                   "l2": f"working set {info['workspace_bytes'] / 1e6:.0f} MB > 129 MB L2, no flush",
+                   "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
+        "e2e": e2e,
+        "gpu_launches": 2 * nlaunch,
+        "roofline": {"kernel": "volume_kernel<4,double>", "bound": "alu", "achieved": achieved_tf,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": None, "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
+                     "avg_launch_ms": 1e3 * vol_avg_s,
+                     "share_of_step": ms_vol / (ms_vol + ms_upd)},
+        "kernels": {"volume_ms_avg": 1e3 * vol_avg_s, "update_ms_avg": ms_upd / nlaunch,
+                    "update_hbm_frac": update_bytes(Nl, Ng, 2 / 3) / (ms_upd * 1e-3 / nlaunch) / 1e9 / hbm_gbs},
+        "clocks": ck,
+        "finite": finite,
+    }
+    if not args.no_fp32:
+        ms32, vol32, upd32, _, _, _, fin32 = measure("fp32_mixed")
+        v32 = world * Ng * STAGES * args.steps / (ms32 * 1e-3)
+        vol32_s = vol32 * 1e-3 / nlaunch
+        b = volume_bytes(Nl, Ng, 4)
+        line["fp32_mixed"] = {
+            "value": v32, "unit": UNIT, "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": v32 / value,
+            "finite": fin32,
+            "roofline": {"kernel": "volume_kernel<4,float>", "bound": "hbm", "achieved": b / vol32_s / 1e9,
+                         "peak": hbm_gbs, "unit": "GB/s", "frac": b / vol32_s / 1e9 / hbm_gbs,
+                         "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
+            "update_ms_avg": upd32 / nlaunch,
+        }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * numa.h -- C ABI of the GB300-native CG spectral-element RHS / Runge-Kutta
+ * hot path of the NUMA dynamical core (Mueller et al., "Strong scaling for
+ * numerical weather prediction at petascale with the atmospheric model
+ * NUMA", Sec. 2 and the main loop of code example 1 in Sec. 6).
+ *
+ * Ownership model
+ *   - The library allocates no device memory.  The caller provides one device
+ *     workspace of numa_get_mesh_info().workspace_bytes bytes and a CUDA
+ *     stream (numa_bind); the library carves geometry, state and scratch out
+ *     of it and enqueues every copy and kernel on that stream.
+ *   - A context owns host-side mesh metadata only; numa_destroy frees it and
+ *     never touches caller memory.
+ *   - Pointers documented as "device" must be device-accessible for the bound
+ *     device; "host" pointers are read or written before the call returns
+ *     unless stated otherwise.
+ *
+ * Errors
+ *   Every call returns an int status: NUMA_OK (0) or a negative NUMA_E* code.
+ *   Nothing aborts, traps or exits.  numa_last_error() returns a message owned
+ *   by the context (valid until the next call on it).
+ *
+ * Data layout (all calls)
+ *   State q and tendency R are double[5][Ng] (structure of arrays), variable
+ *   order (rho', U_x, U_y, U_z, Theta'): density perturbation, momentum
+ *   U = rho u, and rho*theta minus the reference (rho theta)_0 (Eq. 1 in
+ *   perturbation form about a hydrostatic reference state).
+ *   Box meshes number global nodes structurally:
+ *       g = ix + nx * (iy + ny * iz),  nx = nex*N + 1 (walls) or nex*N
+ *       (periodic along x), likewise ny, nz; node (ix, iy, iz) lies at the
+ *       LGL position of lattice index ix along x, etc.
+ *   Shell meshes number global nodes internally; numa_get_coords() returns
+ *   their coordinates.
+ */
+#ifndef NUMA_H
+#define NUMA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NUMA_OK 0
+#define NUMA_EINVAL (-1)     /* bad argument or configuration */
+#define NUMA_ENOMEM (-2)     /* host allocation failed or workspace too small */
+#define NUMA_ECUDA (-3)      /* a CUDA runtime call failed */
+#define NUMA_ENONFINITE (-4) /* the state became non-finite during a step */
+#define NUMA_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define NUMA_EBUDGET (-6)    /* a request does not fit the HBM budget */
+#define NUMA_ESTATE (-7)     /* call made in the wrong order (e.g. before numa_bind) */
+
+enum numa_mesh_kind { NUMA_MESH_BOX = 0, NUMA_MESH_SHELL = 1 };
+enum numa_ref_kind { NUMA_REF_ISENTROPIC = 0, NUMA_REF_ISOTHERMAL = 1 };
+enum numa_precision {
+  NUMA_FP64 = 0,      /* every step in FP64 */
+  NUMA_FP32_MIXED = 1 /* fluxes, metric terms and D contractions in FP32;
+                         state, EOS reference subtraction, DSS, inverse mass
+                         and the RK combination in FP64 */
+};
+enum numa_ic_kind { NUMA_IC_REST = 0, NUMA_IC_BUBBLE = 1, NUMA_IC_UNIFORM = 2, NUMA_IC_JETWAVE = 3 };
+
+/* Mesh, physics and precision.  Sec. 2.1 (order N, Lobatto points), Sec. 3
+ * (the box and the cubed-sphere shell test cases), Sec. 4 (columns of
+ * radial layers). */
+typedef struct {
+  int mesh_kind;           /* numa_mesh_kind */
+  int N;                   /* polynomial order, 1..8 (N+1 LGL points per direction) */
+  int nex, ney, nez;       /* box: elements along x, y, z */
+  double Lx, Ly, Lz;       /* box: extents in m, origin at (0,0,0) */
+  int periodic[3];         /* box: 1 = periodic along that axis, 0 = no-flux walls */
+  double warp;             /* box: amplitude of a smooth interior warp that keeps every
+                              face in place, as a fraction of the extent (0 = affine):
+                              x += warp Lx sin(pi X) sin(pi Y) sin(pi Z),
+                              y += warp Ly sin(2 pi X) sin(pi Y) sin(pi Z),
+                              z += warp Lz sin(pi X) sin(2 pi Y) sin(pi Z), X = x/Lx ... */
+  int npanel, nlayer;      /* shell: columns per cube-panel edge, radial layers */
+  double r_inner, r_outer; /* shell: planet radius a and lid radius, m */
+  double Rd, cp, cv, P00;  /* gas constant, heat capacities, reference pressure */
+  double g;                /* box: gravity; shell: surface gravity g0, g(r) = g0 (a/r)^2 */
+  double Omega;            /* shell: rotation rate about +z, 1/s */
+  int ref_kind;            /* numa_ref_kind of the hydrostatic reference state */
+  double theta0, T0;       /* isentropic potential temperature / isothermal temperature */
+  int precision;           /* numa_precision */
+} numa_config;
+
+typedef struct {
+  long long Ne, Nl, Ng;   /* elements, element-local nodes Ne (N+1)^3, global nodes */
+  size_t workspace_bytes; /* device bytes numa_bind needs */
+  int N;
+} numa_mesh_info;
+
+typedef struct numa_ctx numa_ctx;
+
+/* Build the host mesh: LGL nodes, D, coordinates, isoparametric metric terms
+ * and Jacobian (Eq. 5), Jw, element-to-global map and its inverse, the
+ * diagonal mass matrix M = sum_e Jw (Eq. 4) and the hydrostatic reference
+ * state.  *out receives a new context or NULL on error. */
+int numa_create(const numa_config* cfg, numa_ctx** out);
+
+/* Sizes and the workspace requirement of a context. */
+int numa_get_mesh_info(const numa_ctx* ctx, numa_mesh_info* info);
+
+/* Bind a caller-owned device workspace (>= workspace_bytes, 256-byte aligned)
+ * and a cudaStream_t (passed as void*; NULL = legacy default stream).  Uploads
+ * the geometry into the workspace on that stream and waits for it.  May be
+ * called again to move the context to another workspace or stream. */
+int numa_bind(numa_ctx* ctx, void* dev_workspace, size_t bytes, void* stream);
+
+/* Write an initial state into the context's state (Sec. 3 test cases).
+ * params: REST -; BUBBLE {A, r_c, x_c, y_c, z_c} (cosine potential-
+ * temperature bubble, pressure unperturbed); UNIFORM {u0, v0, w0};
+ * JETWAVE {U_jet, amp, radius/a, lambda_c, phi_c} (zonal jet
+ * U_jet sin^2(2 phi) plus a Gaussian zonal-wind bump). */
+int numa_init_state(numa_ctx* ctx, int ic_kind, const double* params, int nparams);
+
+/* Copy the context's state from / to a caller buffer double[5][Ng];
+ * on_device = 1 for a device pointer, 0 for host memory (pinned memory
+ * makes the copy asynchronous-capable; the call waits for completion). */
+int numa_set_state(numa_ctx* ctx, const double* q, int on_device);
+int numa_get_state(numa_ctx* ctx, double* q, int on_device);
+
+/* R = dq/dt of Eq. 4 at state q: element volume terms, direct stiffness
+ * summation, inverse mass matrix, sources and the no-normal-flow wall
+ * condition.  q_dev, r_dev: device double[5][Ng] (may not alias).  Enqueued
+ * on the bound stream; returns without waiting. */
+int numa_rhs(numa_ctx* ctx, const double* q_dev, double* r_dev);
+
+/* Advance the context's state by one three-stage SSP-RK3 step of size dt
+ * (Sec. 2.2 explicit stages: per stage create_rhs, DSS with the inverse mass
+ * matrix, update q).  Enqueued on the bound stream; returns without waiting. */
+int numa_rk_step(numa_ctx* ctx, double dt);
+
+/* nsteps SSP-RK3 steps (one captured CUDA graph per step, replayed), then
+ * waits for the stream and returns NUMA_ENONFINITE if any stage produced a
+ * non-finite value. */
+int numa_run(numa_ctx* ctx, double dt, int nsteps);
+
+/* Measurement helper: advance the state by nsteps SSP-RK3 steps with plain
+ * (non-graph) launches, bracketing every kernel with CUDA events on the
+ * bound stream, then wait and return the summed device time in ms of the
+ * element volume kernels (*ms_volume) and of the DSS/update kernels
+ * (*ms_update), 3*nsteps launches each. */
+int numa_time_kernels(numa_ctx* ctx, double dt, int nsteps, double* ms_volume, double* ms_update);
+
+/* Non-finite flag raised by any stage update since the last call; resets it.
+ * Waits for the stream. *flag = 0 or 1. */
+int numa_check_finite(numa_ctx* ctx, int* flag);
+
+/* Host copy of the global-node coordinates, double[3][Ng] (x, y, z). */
+int numa_get_coords(const numa_ctx* ctx, double* xyz);
+
+/* Last error message of this context (never NULL). */
+const char* numa_last_error(const numa_ctx* ctx);
+
+/* Free the context's host data.  Never frees the workspace. */
+int numa_destroy(numa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

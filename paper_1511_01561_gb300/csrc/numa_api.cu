@@ -1,0 +1,395 @@
+// C-ABI of the GB300 NUMA hot path (declared in include/numa.h): context
+// life cycle, workspace binding, state I/O and the stage loop of code
+// example 1 in Sec. 6 (create_rhs, DSS with the inverse mass matrix, update
+// q), with one CUDA graph per RK step for numa_run.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "numa_internal.h"
+
+using namespace numa;
+
+struct numa_ctx {
+  numa_config cfg;
+  HostMesh mesh;
+  DevLayout L;
+  bool bound = false;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double gamma = 1.4;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = NAN;
+  const double* graph_q = nullptr;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int fail(numa_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(numa_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, NUMA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// SSP-RK3 stage coefficients: q^{k+1} = a_k q^n + b_k (q^k + dt R(q^k))
+const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0};
+const double kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
+
+VolumeArgs volume_args(const numa_ctx* c, const double* q) {
+  VolumeArgs a;
+  a.q = q;
+  a.ref = c->L.ref;
+  a.l2g = c->L.l2g;
+  a.met64 = c->L.met64;
+  a.met32 = c->L.met32;
+  a.D64 = c->L.D64;
+  a.D32 = c->L.D32;
+  a.re = c->L.re;
+  a.Ng = c->mesh.Ng;
+  a.Nl = c->mesh.Nl;
+  a.Ne = (int)c->mesh.Ne;
+  a.gamma = c->gamma;
+  return a;
+}
+
+UpdateArgs update_args(const numa_ctx* c, const double* qk, const double* qn, double* out, int mode, double ra,
+                       double rb, double dt) {
+  UpdateArgs a;
+  a.off = c->L.csr_off;
+  a.idx = c->L.csr_idx;
+  a.re = c->L.re;
+  a.Minv = c->L.Minv;
+  a.wall = c->L.wall;
+  a.gvec = c->L.gvec;
+  a.nrm = c->L.nrm;
+  a.qk = qk;
+  a.qn = qn;
+  a.out = out;
+  a.Ng = c->mesh.Ng;
+  a.Nl = c->mesh.Nl;
+  a.g = c->cfg.g;
+  a.two_omega = 2.0 * c->cfg.Omega;
+  a.a = ra;
+  a.b = rb;
+  a.dt = dt;
+  a.mode = mode;
+  a.flag = c->L.flags;
+  return a;
+}
+
+// One SSP-RK3 step on stream s: three times (create_rhs; DSS + M^-1 + update q).
+cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s) {
+  double* q = c->L.q;
+  double* qs = c->L.qs;
+  const double* qin[3] = {q, qs, qs};
+  double* qout[3] = {qs, qs, q};
+  for (int st = 0; st < 3; ++st) {
+    cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st]), s);
+    if (e != cudaSuccess) return e;
+    e = launch_update(update_args(c, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt), s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+namespace numa {
+
+size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, DevLayout* L) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off = align_up(off + bytes);
+    return p;
+  };
+  const size_t Ng = (size_t)m.Ng, Nl = (size_t)m.Nl, PP = (size_t)m.P * m.P;
+  DevLayout d;
+  d.flags = (int*)take(64 * sizeof(int));
+  d.q = (double*)take(5 * Ng * 8);
+  d.qs = (double*)take(5 * Ng * 8);
+  d.re = (double*)take(5 * Nl * 8);
+  if (c.precision == NUMA_FP32_MIXED) d.met32 = (float*)take(10 * Nl * 4);
+  else d.met64 = (double*)take(10 * Nl * 8);
+  d.l2g = (int32_t*)take(Nl * 4);
+  d.csr_off = (int32_t*)take((Ng + 1) * 4);
+  d.csr_idx = (int32_t*)take(Nl * 4);
+  d.ref = (double*)take(3 * Ng * 8);
+  d.Minv = (double*)take(Ng * 8);
+  d.wall = (uint8_t*)take(Ng);
+  if (c.mesh_kind == NUMA_MESH_SHELL) {
+    d.gvec = (double*)take(3 * Ng * 8);
+    d.nrm = (double*)take(3 * Ng * 8);
+  }
+  d.D64 = (double*)take(PP * 8);
+  d.D32 = (float*)take(PP * 4);
+  d.bytes = off;
+  if (L) *L = d;
+  return off;
+}
+
+}  // namespace numa
+
+extern "C" {
+
+int numa_create(const numa_config* cfg, numa_ctx** out) {
+  if (!out) return NUMA_EINVAL;
+  *out = nullptr;
+  if (!cfg) return NUMA_EINVAL;
+  if (cfg->precision != NUMA_FP64 && cfg->precision != NUMA_FP32_MIXED) return NUMA_EINVAL;
+  if (!(cfg->cv > 0) || !(cfg->cp > cfg->cv) || !(cfg->Rd > 0) || !(cfg->P00 > 0)) return NUMA_EINVAL;
+  numa_ctx* c = new (std::nothrow) numa_ctx();
+  if (!c) return NUMA_ENOMEM;
+  c->cfg = *cfg;
+  c->gamma = cfg->cp / cfg->cv;
+  try {
+    if (!build_host_mesh(c->cfg, c->mesh, c->err)) {
+      delete c;
+      return NUMA_EINVAL;
+    }
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return NUMA_ENOMEM;
+  }
+  *out = c;
+  return NUMA_OK;
+}
+
+int numa_get_mesh_info(const numa_ctx* c, numa_mesh_info* info) {
+  if (!c || !info) return NUMA_EINVAL;
+  info->Ne = c->mesh.Ne;
+  info->Nl = c->mesh.Nl;
+  info->Ng = c->mesh.Ng;
+  info->N = c->mesh.N;
+  info->workspace_bytes = layout_workspace(c->cfg, c->mesh, nullptr, nullptr);
+  return NUMA_OK;
+}
+
+int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
+  if (!c) return NUMA_EINVAL;
+  if (!ws) return fail(c, NUMA_EINVAL, "workspace is NULL");
+  if (((uintptr_t)ws) % kAlign) return fail(c, NUMA_EINVAL, "workspace must be 256-byte aligned");
+  size_t need = layout_workspace(c->cfg, c->mesh, nullptr, nullptr);
+  if (bytes < need) return fail(c, NUMA_ENOMEM, "workspace smaller than workspace_bytes");
+  DevLayout L;
+  layout_workspace(c->cfg, c->mesh, (char*)ws, &L);
+  cudaStream_t s = (cudaStream_t)stream;
+  const HostMesh& m = c->mesh;
+  const size_t Ng = (size_t)m.Ng, Nl = (size_t)m.Nl;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t n) {
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+  };
+  std::vector<float> met32, D32;
+  if (c->cfg.precision == NUMA_FP32_MIXED) {
+    met32.resize(m.met.size());
+    for (size_t t = 0; t < m.met.size(); ++t) met32[t] = (float)m.met[t];
+    up(L.met32, met32.data(), met32.size() * 4);
+  } else {
+    up(L.met64, m.met.data(), m.met.size() * 8);
+  }
+  D32.resize(m.D.size());
+  for (size_t t = 0; t < m.D.size(); ++t) D32[t] = (float)m.D[t];
+  up(L.D64, m.D.data(), m.D.size() * 8);
+  up(L.D32, D32.data(), D32.size() * 4);
+  up(L.l2g, m.l2g.data(), Nl * 4);
+  up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
+  up(L.csr_idx, m.csr_idx.data(), Nl * 4);
+  up(L.ref, m.ref.data(), 3 * Ng * 8);
+  up(L.Minv, m.Minv.data(), Ng * 8);
+  up(L.wall, m.wall.data(), Ng);
+  if (L.gvec) up(L.gvec, m.gvec.data(), 3 * Ng * 8);
+  if (L.nrm) up(L.nrm, m.nrm.data(), 3 * Ng * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.flags, 0, 64 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.q, 0, 5 * Ng * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.qs, 0, 5 * Ng * 8, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind upload");
+  // kernel attributes are set outside any stream capture
+  VolumeArgs probe = volume_args(c, L.q);
+  probe.Ne = 0;
+  e = launch_volume(m.N, c->cfg.precision, probe, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind kernel setup");
+  c->L = L;
+  c->stream = s;
+  c->bound = true;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return NUMA_OK;
+}
+
+int numa_init_state(numa_ctx* c, int kind, const double* params, int nparams) {
+  if (!c) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_init_state before numa_bind");
+  if (nparams < 0 || (nparams > 0 && !params)) return fail(c, NUMA_EINVAL, "bad params");
+  std::vector<double> q;
+  try {
+    q.resize(5 * (size_t)c->mesh.Ng);
+  } catch (const std::bad_alloc&) {
+    return fail(c, NUMA_ENOMEM, "host allocation");
+  }
+  if (!init_state_host(c->cfg, c->mesh, kind, params, nparams, q.data(), c->err)) return NUMA_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(c->L.q, q.data(), q.size() * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_init_state upload");
+  return NUMA_OK;
+}
+
+int numa_set_state(numa_ctx* c, const double* q, int on_device) {
+  if (!c || !q) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_set_state before numa_bind");
+  cudaError_t e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_set_state");
+  return NUMA_OK;
+}
+
+int numa_get_state(numa_ctx* c, double* q, int on_device) {
+  if (!c || !q) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_get_state before numa_bind");
+  cudaError_t e = cudaMemcpyAsync(q, c->L.q, 5 * (size_t)c->mesh.Ng * 8,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_get_state");
+  return NUMA_OK;
+}
+
+int numa_rhs(numa_ctx* c, const double* q_dev, double* r_dev) {
+  if (!c || !q_dev || !r_dev) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rhs before numa_bind");
+  if ((const void*)q_dev == (const void*)r_dev) return fail(c, NUMA_EINVAL, "q and r must not alias");
+  cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, q_dev), c->stream);
+  if (e == cudaSuccess) e = launch_update(update_args(c, q_dev, q_dev, r_dev, 0, 0.0, 1.0, 0.0), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_rhs launch");
+  return NUMA_OK;
+}
+
+int numa_rk_step(numa_ctx* c, double dt) {
+  if (!c) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rk_step before numa_bind");
+  if (!std::isfinite(dt)) return fail(c, NUMA_EINVAL, "dt must be finite");
+  cudaError_t e = enqueue_rk_step(c, dt, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_rk_step launch");
+  return NUMA_OK;
+}
+
+int numa_run(numa_ctx* c, double dt, int nsteps) {
+  if (!c) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_run before numa_bind");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NUMA_EINVAL, "bad nsteps or dt");
+  cudaError_t e = cudaSuccess;
+  if (!c->graph || c->graph_dt != dt || c->graph_q != c->L.q) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = enqueue_rk_step(c, dt, c->cap_stream);
+      e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_run graph capture");
+    c->graph_dt = dt;
+    c->graph_q = c->L.q;
+  }
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = cudaGraphLaunch(c->graph, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_run graph launch");
+  int flag = 0;
+  int rc = numa_check_finite(c, &flag);
+  if (rc != NUMA_OK) return rc;
+  if (flag) return fail(c, NUMA_ENONFINITE, "non-finite state");
+  return NUMA_OK;
+}
+
+int numa_time_kernels(numa_ctx* c, double dt, int nsteps, double* ms_volume, double* ms_update) {
+  if (!c || !ms_volume || !ms_update) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_time_kernels before numa_bind");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NUMA_EINVAL, "bad nsteps or dt");
+  const int nk = 3 * nsteps;
+  std::vector<cudaEvent_t> ev(4 * (size_t)nk, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  double* q = c->L.q;
+  double* qs = c->L.qs;
+  const double* qin[3] = {q, qs, qs};
+  double* qout[3] = {qs, qs, q};
+  for (int t = 0; t < nk && e == cudaSuccess; ++t) {
+    const int st = t % 3;
+    cudaEvent_t* E = &ev[4 * (size_t)t];
+    e = cudaEventRecord(E[0], c->stream);
+    if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st]), c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[1], c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[2], c->stream);
+    if (e == cudaSuccess)
+      e = launch_update(update_args(c, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt), c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[3], c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  double tv = 0.0, tu = 0.0;
+  for (int t = 0; t < nk && e == cudaSuccess; ++t) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, ev[4 * (size_t)t], ev[4 * (size_t)t + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * (size_t)t + 2], ev[4 * (size_t)t + 3]);
+    tv += a;
+    tu += b;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_time_kernels");
+  *ms_volume = tv;
+  *ms_update = tu;
+  return NUMA_OK;
+}
+
+int numa_check_finite(numa_ctx* c, int* flag) {
+  if (!c || !flag) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_check_finite before numa_bind");
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->L.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && h) e = cudaMemsetAsync(c->L.flags, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_check_finite");
+  *flag = h ? 1 : 0;
+  return NUMA_OK;
+}
+
+int numa_get_coords(const numa_ctx* c, double* xyz) {
+  if (!c || !xyz) return NUMA_EINVAL;
+  std::memcpy(xyz, c->mesh.gxyz.data(), c->mesh.gxyz.size() * sizeof(double));
+  return NUMA_OK;
+}
+
+const char* numa_last_error(const numa_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+int numa_destroy(numa_ctx* c) {
+  if (!c) return NUMA_EINVAL;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+  return NUMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Internal declarations of the GB300 NUMA hot-path library: host mesh data,
+// the device workspace layout and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "numa.h"
+
+namespace numa {
+
+constexpr int kMaxN = 8;
+
+// Host-side mesh and geometry (Sec. 2.1: Lobatto points, Eq. 4: Jw and M,
+// Eq. 5: isoparametric metric terms).  Built once per context.
+struct HostMesh {
+  int N = 0, P = 0, Np = 0;
+  long long Ne = 0, Nl = 0, Ng = 0;
+  std::vector<double> xi, w, D;       // 1D Lobatto nodes, weights, D[i*P+j] = psi_j'(xi_i)
+  std::vector<double> gxyz;           // global-node coordinates [3][Ng]
+  std::vector<int32_t> l2g;           // element node -> global node [Nl]
+  std::vector<int32_t> csr_off;       // global node -> first entry in csr_idx [Ng+1]
+  std::vector<int32_t> csr_idx;       // element nodes of each global node, ascending [Nl]
+  std::vector<double> met;            // [10][Nl]: dxi_d/dx_c at row 3d+c, then Jw
+  std::vector<double> ref;            // [3][Ng]: rho0, (rho theta)_0, p0
+  std::vector<double> Minv;           // [Ng]: 1 / sum_e Jw
+  std::vector<uint8_t> wall;          // [Ng]: bit a = box wall normal to axis a; bit 3 = shell radial wall
+  std::vector<double> gvec;           // shell only, [3][Ng]: g(r) r_hat
+  std::vector<double> nrm;            // shell only, [3][Ng]: r_hat (wall normal)
+};
+
+bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err);
+bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const double* prm, int nprm,
+                     double* q, std::string& err);
+
+// Device workspace carved from the caller's buffer.
+struct DevLayout {
+  double* q = nullptr;       // state q^n [5][Ng]
+  double* qs = nullptr;      // stage state [5][Ng]
+  double* re = nullptr;      // element-local residuals -Jw div F [5][Nl] (scratch)
+  double* met64 = nullptr;   // [10][Nl] FP64 metric terms and Jw
+  float* met32 = nullptr;    // [10][Nl] FP32 copy (mixed-precision form)
+  int32_t* l2g = nullptr;
+  int32_t* csr_off = nullptr;
+  int32_t* csr_idx = nullptr;
+  double* ref = nullptr;     // [3][Ng]
+  double* Minv = nullptr;    // [Ng]
+  uint8_t* wall = nullptr;   // [Ng]
+  double* gvec = nullptr;    // [3][Ng] (shell)
+  double* nrm = nullptr;     // [3][Ng] (shell)
+  double* D64 = nullptr;     // [P*P]
+  float* D32 = nullptr;      // [P*P]
+  int* flags = nullptr;      // [64]: 0 = non-finite
+  size_t bytes = 0;
+};
+
+size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, DevLayout* L);
+
+// ---- kernels -------------------------------------------------------------
+
+struct VolumeArgs {
+  const double* q;    // state [5][Ng]
+  const double* ref;  // [3][Ng]
+  const int32_t* l2g;
+  const double* met64;
+  const float* met32;
+  const double* D64;
+  const float* D32;
+  double* re;         // [5][Nl]
+  long long Ng, Nl;
+  int Ne;
+  double gamma;
+};
+
+struct UpdateArgs {
+  const int32_t* off;
+  const int32_t* idx;
+  const double* re;
+  const double* Minv;
+  const uint8_t* wall;
+  const double* gvec;  // shell gravity vectors or null (box)
+  const double* nrm;   // shell radial unit vectors (read at wall nodes)
+  const double* qk;    // state the RHS was evaluated at
+  const double* qn;    // q^n (RK base), may equal qk
+  double* out;         // R (mode 0) or q^{k+1} (mode 1)
+  long long Ng, Nl;
+  double g;            // box gravity
+  double two_omega;    // shell Coriolis 2 Omega
+  double a, b, dt;     // out = a qn + b (qk + dt R)
+  int mode;            // 0: write R, 1: RK stage
+  int* flag;           // non-finite flag
+};
+
+cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+
+}  // namespace numa

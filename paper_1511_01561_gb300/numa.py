@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C ABI in ``include/numa.h``.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library ``libnuma_gb300.so``.  Importing this module loads the library and
+raises ``ImportError`` if it has not been built -- there is no CPU fallback.
+PyTorch is used for device memory (the workspace) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnuma_gb300.so")
+
+NUMA_OK = 0
+ERRORS = {-1: "NUMA_EINVAL", -2: "NUMA_ENOMEM", -3: "NUMA_ECUDA", -4: "NUMA_ENONFINITE",
+          -5: "NUMA_ETIMEOUT", -6: "NUMA_EBUDGET", -7: "NUMA_ESTATE"}
+MESH = {"box": 0, "shell": 1}
+REF = {"isentropic": 0, "isothermal": 1}
+PRECISION = {"fp64": 0, "fp32_mixed": 1}
+IC = {"rest": 0, "bubble": 1, "uniform": 2, "jetwave": 3}
+
+
+class NumaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class numa_config(ctypes.Structure):
+    _fields_ = [
+        ("mesh_kind", ctypes.c_int), ("N", ctypes.c_int),
+        ("nex", ctypes.c_int), ("ney", ctypes.c_int), ("nez", ctypes.c_int),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+        ("periodic", ctypes.c_int * 3), ("warp", ctypes.c_double),
+        ("npanel", ctypes.c_int), ("nlayer", ctypes.c_int),
+        ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double),
+        ("Rd", ctypes.c_double), ("cp", ctypes.c_double), ("cv", ctypes.c_double),
+        ("P00", ctypes.c_double), ("g", ctypes.c_double), ("Omega", ctypes.c_double),
+        ("ref_kind", ctypes.c_int), ("theta0", ctypes.c_double), ("T0", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class numa_mesh_info(ctypes.Structure):
+    _fields_ = [("Ne", ctypes.c_longlong), ("Nl", ctypes.c_longlong), ("Ng", ctypes.c_longlong),
+                ("workspace_bytes", ctypes.c_size_t), ("N", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1511_01561_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+    sig = {
+        "numa_create": [ctypes.POINTER(numa_config), ctypes.POINTER(vp)],
+        "numa_get_mesh_info": [vp, ctypes.POINTER(numa_mesh_info)],
+        "numa_bind": [vp, vp, ctypes.c_size_t, vp],
+        "numa_init_state": [vp, i, dp, i],
+        "numa_set_state": [vp, vp, i],
+        "numa_get_state": [vp, vp, i],
+        "numa_rhs": [vp, vp, vp],
+        "numa_rk_step": [vp, d],
+        "numa_run": [vp, d, i],
+        "numa_check_finite": [vp, ctypes.POINTER(i)],
+        "numa_time_kernels": [vp, d, i, dp, dp],
+        "numa_get_coords": [vp, dp],
+        "numa_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.numa_last_error.argtypes = [vp]
+    L.numa_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(ctx, rc: int):
+    if rc != NUMA_OK:
+        msg = lib.numa_last_error(ctx).decode() if ctx else ""
+        raise NumaError(rc, msg)
+
+
+def make_config(cfg: dict, precision: str = "fp64") -> numa_config:
+    c = numa_config()
+    c.mesh_kind = MESH[cfg["kind"]]
+    c.N = int(cfg["N"])
+    c.nex, c.ney, c.nez = (int(v) for v in cfg.get("ne", (1, 1, 1)))
+    c.Lx, c.Ly, c.Lz = (float(v) for v in cfg.get("L", (1.0, 1.0, 1.0)))
+    for a, p in enumerate(cfg.get("periodic", (0, 0, 0))):
+        c.periodic[a] = int(bool(p))
+    c.warp = float(cfg.get("warp", 0.0))
+    c.npanel = int(cfg.get("npanel", 0))
+    c.nlayer = int(cfg.get("nlayer", 0))
+    c.r_inner = float(cfg.get("r_inner", 0.0))
+    c.r_outer = float(cfg.get("r_outer", 0.0))
+    c.Rd, c.cp, c.cv, c.P00 = (float(cfg[k]) for k in ("Rd", "cp", "cv", "P00"))
+    c.g = float(cfg["g"])
+    c.Omega = float(cfg.get("Omega", 0.0))
+    c.ref_kind = REF[cfg.get("ref", "isentropic")]
+    c.theta0 = float(cfg.get("theta0", 300.0))
+    c.T0 = float(cfg.get("T0", 300.0))
+    c.precision = PRECISION[cfg.get("precision", precision)]
+    return c
+
+
+# ---- C-ABI calls, same names as include/numa.h ---------------------------
+
+def numa_create(cfg: dict, precision: str = "fp64") -> ctypes.c_void_p:
+    c = make_config(cfg, precision)
+    h = ctypes.c_void_p()
+    rc = lib.numa_create(ctypes.byref(c), ctypes.byref(h))
+    if rc != NUMA_OK:
+        raise NumaError(rc, "numa_create")
+    return h
+
+
+def numa_get_mesh_info(ctx) -> dict:
+    info = numa_mesh_info()
+    _check(ctx, lib.numa_get_mesh_info(ctx, ctypes.byref(info)))
+    return dict(Ne=info.Ne, Nl=info.Nl, Ng=info.Ng, workspace_bytes=info.workspace_bytes, N=info.N)
+
+
+def numa_bind(ctx, workspace_ptr: int, nbytes: int, stream_ptr: int) -> None:
+    _check(ctx, lib.numa_bind(ctx, ctypes.c_void_p(workspace_ptr), nbytes, ctypes.c_void_p(stream_ptr)))
+
+
+def numa_init_state(ctx, kind: str, params=()) -> None:
+    p = (ctypes.c_double * max(1, len(params)))(*params)
+    _check(ctx, lib.numa_init_state(ctx, IC[kind], p, len(params)))
+
+
+def numa_set_state(ctx, ptr: int, on_device: bool) -> None:
+    _check(ctx, lib.numa_set_state(ctx, ctypes.c_void_p(ptr), int(on_device)))
+
+
+def numa_get_state(ctx, ptr: int, on_device: bool) -> None:
+    _check(ctx, lib.numa_get_state(ctx, ctypes.c_void_p(ptr), int(on_device)))
+
+
+def numa_rhs(ctx, q_ptr: int, r_ptr: int) -> None:
+    _check(ctx, lib.numa_rhs(ctx, ctypes.c_void_p(q_ptr), ctypes.c_void_p(r_ptr)))
+
+
+def numa_rk_step(ctx, dt: float) -> None:
+    _check(ctx, lib.numa_rk_step(ctx, dt))
+
+
+def numa_run(ctx, dt: float, nsteps: int) -> None:
+    _check(ctx, lib.numa_run(ctx, dt, nsteps))
+
+
+def numa_time_kernels(ctx, dt: float, nsteps: int):
+    """(ms of volume kernels, ms of DSS/update kernels) over nsteps RK3 steps."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib.numa_time_kernels(ctx, dt, nsteps, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def numa_check_finite(ctx) -> int:
+    f = ctypes.c_int()
+    _check(ctx, lib.numa_check_finite(ctx, ctypes.byref(f)))
+    return f.value
+
+
+def numa_get_coords(ctx) -> np.ndarray:
+    ng = numa_get_mesh_info(ctx)["Ng"]
+    a = np.zeros((3, ng))
+    _check(ctx, lib.numa_get_coords(ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return a
+
+
+def numa_last_error(ctx) -> str:
+    return lib.numa_last_error(ctx).decode()
+
+
+def numa_destroy(ctx) -> None:
+    _check(None, lib.numa_destroy(ctx))
+
+
+# ---- convenience wrapper: torch owns the workspace and the stream ----------
+
+class Solver:
+    """One bound context: a device workspace allocated by torch on `device`
+    and the current torch stream of that device."""
+
+    def __init__(self, cfg: dict, precision: str = "fp64", device: str = "cuda:0", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.ctx = numa_create(cfg, precision)
+        self.info = numa_get_mesh_info(self.ctx)
+        self.Ng = int(self.info["Ng"])
+        self.precision = precision
+        self.workspace = torch.empty(self.info["workspace_bytes"] + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        numa_bind(self.ctx, self._ws_ptr, self.info["workspace_bytes"], self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            numa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coords(self) -> np.ndarray:
+        return numa_get_coords(self.ctx)
+
+    def init_state(self, kind: str, params=()):
+        numa_init_state(self.ctx, kind, params)
+
+    def set_state(self, q):
+        t = self.torch
+        if isinstance(q, np.ndarray):
+            q = t.from_numpy(np.ascontiguousarray(q, dtype=np.float64))
+        q = q.contiguous()
+        assert q.dtype == t.float64 and q.numel() == 5 * self.Ng
+        numa_set_state(self.ctx, q.data_ptr(), q.is_cuda)
+
+    def get_state(self, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty((5, self.Ng), dtype=t.float64)
+        numa_get_state(self.ctx, out.data_ptr(), out.is_cuda)
+        return out
+
+    def rhs(self, q, out=None):
+        t = self.torch
+        if isinstance(q, np.ndarray):
+            q = t.from_numpy(np.ascontiguousarray(q, dtype=np.float64))
+        q = q.to(self.device, dtype=t.float64).contiguous()
+        if out is None:
+            out = t.empty((5, self.Ng), dtype=t.float64, device=self.device)
+        numa_rhs(self.ctx, q.data_ptr(), out.data_ptr())
+        return out
+
+    def rk_step(self, dt: float):
+        numa_rk_step(self.ctx, dt)
+
+    def run(self, dt: float, nsteps: int):
+        numa_run(self.ctx, dt, nsteps)
+
+    def time_kernels(self, dt: float, nsteps: int):
+        return numa_time_kernels(self.ctx, dt, nsteps)
+
+    def check_finite(self) -> int:
+        return numa_check_finite(self.ctx)

@@ -1,0 +1,104 @@
+"""CPU checks of the C-ABI library: it loads, exports every function that
+include/numa.h declares, validates arguments without a GPU, and its host mesh
+setup agrees with the oracle's node coordinates."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1511_01561_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def numa():
+    from paper_1511_01561_gb300 import build
+    build.build()
+    from paper_1511_01561_gb300 import numa as mod
+    return mod
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(numa_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(numa):
+    names = _declared("numa.h")
+    assert "numa_rhs" in names and "numa_run" in names
+    for n in names:
+        assert hasattr(numa.lib, n), n
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        for n in _declared(h):
+            assert hasattr(numa.lib, n), (h, n)
+
+
+def test_config_struct_matches_header(numa):
+    src = open(os.path.join(ROOT, "include", "numa.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} numa_config;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1]
+        for nm in names.split(","):
+            fields.append(re.sub(r"\[.*\]", "", nm).strip())
+    assert fields == [f[0] for f in numa.numa_config._fields_]
+
+
+@pytest.mark.parametrize("cfg", [I.box((3, 2, 4), 4), I.box((2, 3, 2), 3, periodic=(1, 0, 1), warp=0.05)])
+def test_host_mesh_matches_oracle_coordinates(numa, orc, cfg):
+    ctx = numa.numa_create(cfg)
+    try:
+        info = numa.numa_get_mesh_info(ctx)
+        m = orc.Mesh(cfg)
+        assert (info["Ne"], info["Nl"], info["Ng"]) == (m.Ne, m.Nl, m.Ng)
+        assert np.abs(numa.numa_get_coords(ctx) - m.coords()).max() < 1e-9
+    finally:
+        numa.numa_destroy(ctx)
+
+
+def test_shell_sizes_match_oracle(numa, orc):
+    cfg = I.shell(3, 2, 3)
+    ctx = numa.numa_create(cfg)
+    try:
+        info = numa.numa_get_mesh_info(ctx)
+        m = orc.Mesh(cfg)
+        assert (info["Ne"], info["Nl"], info["Ng"]) == (m.Ne, m.Nl, m.Ng)
+        a = numa.numa_get_coords(ctx)
+        b = m.coords()
+        ka = np.lexsort(np.round(a / 1e-3))
+        kb = np.lexsort(np.round(b / 1e-3))
+        assert np.abs(a[:, ka] - b[:, kb]).max() < 1e-6
+    finally:
+        numa.numa_destroy(ctx)
+
+
+def test_argument_errors_without_gpu(numa):
+    with pytest.raises(numa.NumaError) as e:
+        numa.numa_create(I.box(2, 9))
+    assert e.value.code == -1
+    with pytest.raises(numa.NumaError):
+        numa.numa_create(I.box(0, 4))
+    ctx = numa.numa_create(I.box(2, 2))
+    try:
+        with pytest.raises(numa.NumaError) as e:
+            numa.numa_rhs(ctx, 256, 512)
+        assert e.value.code == -7  # NUMA_ESTATE: not bound
+        with pytest.raises(numa.NumaError) as e:
+            numa.numa_bind(ctx, 0, 1 << 20, 0)
+        assert e.value.code == -1
+        with pytest.raises(numa.NumaError) as e:
+            numa.numa_bind(ctx, 256, 16, 0)
+        assert e.value.code == -2  # workspace too small
+        assert "workspace" in numa.numa_last_error(ctx)
+    finally:
+        numa.numa_destroy(ctx)
+    assert numa.lib.numa_destroy(None) == -1
+    assert numa.lib.numa_rhs(None, None, None) == -1
