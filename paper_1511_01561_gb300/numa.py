@@ -243,8 +243,12 @@ class Solver:
         if isinstance(q, np.ndarray):
             q = t.from_numpy(np.ascontiguousarray(q, dtype=np.float64))
         q = q.to(self.device, dtype=t.float64).contiguous()
+        if q.numel() != 5 * self.Ng:
+            raise ValueError(f"state must hold 5*Ng = {5 * self.Ng} values")
         if out is None:
             out = t.empty((5, self.Ng), dtype=t.float64, device=self.device)
+        if out.numel() != 5 * self.Ng or not out.is_cuda or out.dtype != t.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 CUDA tensor of 5*Ng values")
         numa_rhs(self.ctx, q.data_ptr(), out.data_ptr())
         return out
 
