@@ -46,6 +46,7 @@ struct orc_mesh {
   double *ex, *ey, *ez; /* element-node coordinates [Nl] */
   long* l2g;            /* element node -> global node [Nl] */
   double *gx, *gy, *gz; /* global-node coordinates [Ng] */
+  double* gh;           /* shell: height of the global node above r_inner [Ng] */
   double* dxi;          /* dxi_d/dx_c at [n*9 + d*3 + c] */
   double* J;            /* Jacobian determinant [Nl] */
   double* Jw;           /* J w_i w_j w_k [Nl] */
@@ -139,7 +140,7 @@ static void* xalloc(size_t n) { return calloc(n ? n : 1, 1); }
 void orc_free(orc_mesh* m) {
   if (!m) return;
   free(m->ex); free(m->ey); free(m->ez); free(m->l2g);
-  free(m->gx); free(m->gy); free(m->gz); free(m->dxi); free(m->J); free(m->Jw);
+  free(m->gx); free(m->gy); free(m->gz); free(m->gh); free(m->dxi); free(m->J); free(m->Jw);
   free(m->M); free(m->rho0); free(m->Th0); free(m->p0); free(m->wall);
   free(m);
 }
@@ -337,9 +338,10 @@ static int build_shell(orc_mesh* m) {
   m->gx = xalloc(sizeof(double) * Ng);
   m->gy = xalloc(sizeof(double) * Ng);
   m->gz = xalloc(sizeof(double) * Ng);
+  m->gh = xalloc(sizeof(double) * Ng);
   m->wall = xalloc(Ng);
   unsigned char* seen = xalloc(Ng);
-  if (!m->gx || !m->gy || !m->gz || !m->wall || !seen) {
+  if (!m->gx || !m->gy || !m->gz || !m->gh || !m->wall || !seen) {
     free(seen);
     return -2;
   }
@@ -355,6 +357,7 @@ static int build_shell(orc_mesh* m) {
             m->gx[g] = m->ex[n];
             m->gy[g] = m->ey[n];
             m->gz[g] = m->ez[n];
+            m->gh[g] = (il + 0.5 * (m->xi[k] + 1.0)) * (c->r_outer - c->r_inner) / nl;
           }
           if ((il == 0 && k == 0) || (il == nl - 1 && k == N)) m->wall[g] = 8;
         }
@@ -417,13 +420,15 @@ static int build_metrics(orc_mesh* m) {
   return 0;
 }
 
-/* Geopotential of the node: g z in the box, g0 a (1 - a/r) on the shell
- * (deep atmosphere, g(r) = g0 (a/r)^2). */
+/* Geopotential of the node: g z in the box; on the shell the potential of
+ * the deep-atmosphere gravity g(r) = g0 (a/r)^2, g0 a (1 - a/r), written as
+ * g0 a h / (a + h) with the node height h = r - a taken from the layer
+ * construction (no cancellation of 1 - a/r). */
 static double geopotential(const orc_mesh* m, long g) {
   const orc_config* c = &m->c;
   if (c->kind == ORC_BOX) return c->g * m->gz[g];
-  double r = sqrt(m->gx[g] * m->gx[g] + m->gy[g] * m->gy[g] + m->gz[g] * m->gz[g]);
-  return c->g * c->r_inner * (1.0 - c->r_inner / r);
+  double h = m->gh[g];
+  return c->g * c->r_inner * h / (c->r_inner + h);
 }
 
 /* Hydrostatic reference state per global node.

@@ -149,6 +149,7 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
   m.Ne = 6LL * np * np * nl;
   m.Nl = m.Ne * m.Np;
   X.assign(3 * m.Nl, 0.0);
+  m.hgt.assign(m.Nl, 0.0);
   std::vector<long long> key(m.Nl);
   const double dA = 0.5 * kPi / np, dR = (c.r_outer - c.r_inner) / nl;
   for (int p = 0; p < 6; ++p)
@@ -162,7 +163,9 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
                 long long n = e * m.Np + i + P * (j + P * k);
                 double al = -0.25 * kPi + (ia + 0.5 * (1.0 + m.xi[i])) * dA;
                 double be = -0.25 * kPi + (ib + 0.5 * (1.0 + m.xi[j])) * dA;
-                double r = c.r_inner + (il + 0.5 * (1.0 + m.xi[k])) * dR;
+                const double h = (il + 0.5 * (1.0 + m.xi[k])) * dR;
+                double r = c.r_inner + h;
+                m.hgt[n] = h;
                 double ta = std::tan(al), tb = std::tan(be), v[3], nn = 0.0;
                 for (int d = 0; d < 3; ++d) {
                   v[d] = kFrame[p][2][d] + ta * kFrame[p][0][d] + tb * kFrame[p][1][d];
@@ -246,6 +249,8 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
   const long long Nl = m.Nl, Ng = m.Ng;
   // global coordinates: first element node that maps to each global node
   m.gxyz.assign(3 * Ng, 0.0);
+  std::vector<double> gh;  // shell: node height above r_inner, from the layer construction
+  if (c.mesh_kind == NUMA_MESH_SHELL) gh.assign(Ng, 0.0);
   {
     std::vector<uint8_t> seen(Ng, 0);
     for (long long n = 0; n < Nl; ++n) {
@@ -253,8 +258,10 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
       if (seen[g]) continue;
       seen[g] = 1;
       for (int d = 0; d < 3; ++d) m.gxyz[d * Ng + g] = X[d * Nl + n];
+      if (!gh.empty()) gh[g] = m.hgt[n];
     }
   }
+  std::vector<double>().swap(m.hgt);
   // Eq. 5 metric terms: dx_c/dxi_d = sum_m D x_c along direction d, then the
   // analytic inverse of the 3x3 Jacobian matrix; Jw = det * w_i w_j w_k.
   m.met.assign(10 * Nl, 0.0);
@@ -330,7 +337,9 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
       phi = c.g * z;
     } else {
       double r = std::sqrt(x * x + y * y + z * z);
-      phi = c.g * c.r_inner * (1.0 - c.r_inner / r);
+      // potential of g(r) = g0 (a/r)^2: g0 a (1 - a/r) = g0 a h / (a + h),
+      // with the height h taken from the layer construction (no cancellation)
+      phi = c.g * c.r_inner * gh[g] / (c.r_inner + gh[g]);
       double gr = c.g * (c.r_inner / r) * (c.r_inner / r);
       m.gvec[g] = gr * x / r;
       m.gvec[Ng + g] = gr * y / r;

@@ -30,6 +30,7 @@ struct HostMesh {
   std::vector<uint8_t> wall;          // [Ng]: bit a = box wall normal to axis a; bit 3 = shell radial wall
   std::vector<double> gvec;           // shell only, [3][Ng]: g(r) r_hat
   std::vector<double> nrm;            // shell only, [3][Ng]: r_hat (wall normal)
+  std::vector<double> hgt;            // shell only, [Nl] during setup: height above r_inner
 };
 
 bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err);
