@@ -138,6 +138,26 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   return off;
 }
 
+// RHS with a caller-chosen residual scratch (used by numa_rhs_static_scratch).
+int rhs_with_scratch(numa_ctx* c, const double* q_dev, double* r_dev, double* re_scratch,
+                     long long scratch_doubles) {
+  if (!c || !q_dev || !r_dev || !re_scratch) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rhs_static_scratch before numa_bind");
+  if ((const void*)q_dev == (const void*)r_dev) return fail(c, NUMA_EINVAL, "q and r must not alias");
+  if (5 * c->mesh.Nl > scratch_doubles)
+    return fail(c, NUMA_EINVAL, "mesh needs " + std::to_string(40 * c->mesh.Nl) +
+                                    " bytes of residual scratch; the static array holds " +
+                                    std::to_string(8 * scratch_doubles));
+  VolumeArgs va = volume_args(c, q_dev);
+  va.re = re_scratch;
+  UpdateArgs ua = update_args(c, q_dev, q_dev, r_dev, 0, 0.0, 1.0, 0.0);
+  ua.re = re_scratch;
+  cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, va, c->stream);
+  if (e == cudaSuccess) e = launch_update(ua, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_rhs_static_scratch launch");
+  return NUMA_OK;
+}
+
 }  // namespace numa
 
 extern "C" {

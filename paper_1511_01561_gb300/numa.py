@@ -63,6 +63,7 @@ def _load():
         "numa_set_state": [vp, vp, i],
         "numa_get_state": [vp, vp, i],
         "numa_rhs": [vp, vp, vp],
+        "numa_rhs_static_scratch": [vp, vp, vp],
         "numa_rk_step": [vp, d],
         "numa_run": [vp, d, i],
         "numa_check_finite": [vp, ctypes.POINTER(i)],
@@ -147,6 +148,12 @@ def numa_get_state(ctx, ptr: int, on_device: bool) -> None:
 
 def numa_rhs(ctx, q_ptr: int, r_ptr: int) -> None:
     _check(ctx, lib.numa_rhs(ctx, ctypes.c_void_p(q_ptr), ctypes.c_void_p(r_ptr)))
+
+
+def numa_rhs_static_scratch(ctx, q_ptr: int, r_ptr: int) -> None:
+    """numa_rhs with its residual scratch in the library's fixed device array
+    (for callers that cannot allocate device memory)."""
+    _check(ctx, lib.numa_rhs_static_scratch(ctx, ctypes.c_void_p(q_ptr), ctypes.c_void_p(r_ptr)))
 
 
 def numa_rk_step(ctx, dt: float) -> None:
