@@ -368,9 +368,10 @@ static int build_shell(orc_mesh* m) {
 
 /* Eq. 5 metric terms: x_xi etc. by the isoparametric derivative of the node
  * coordinates with D, then J = det(dx/dxi) and dxi/dx as the 3x3 inverse.
- * D annihilates constants (D 1 = 0), so the coordinates are differentiated
- * relative to the element's first node: the same metric terms, without the
- * rounding of large absolute coordinates (6.4e6 m on the shell). */
+ * D annihilates constants (D 1 = 0), so along each 1D line of nodes the
+ * coordinates are differentiated relative to the line's first node: the same
+ * metric terms, without the rounding of large absolute coordinates (6.4e6 m
+ * on the shell, 9e6 m across one element of a coarse cubed sphere). */
 static int build_metrics(orc_mesh* m) {
   int P = m->P;
   long Np = m->Np;
@@ -387,11 +388,12 @@ static int build_metrics(orc_mesh* m) {
           double A[3][3]; /* A[c][d] = d x_c / d xi_d */
           for (int cc = 0; cc < 3; ++cc) {
             double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-            double x0 = X[cc][e * Np];
+            const double* xe = &X[cc][e * Np];
+            double x0 = xe[P * (j + P * k)], y0 = xe[i + P * P * k], z0 = xe[i + P * j];
             for (int mm = 0; mm < P; ++mm) {
-              s0 += m->D[i * P + mm] * (X[cc][e * Np + mm + P * (j + P * k)] - x0);
-              s1 += m->D[j * P + mm] * (X[cc][e * Np + i + P * (mm + P * k)] - x0);
-              s2 += m->D[k * P + mm] * (X[cc][e * Np + i + P * (j + P * mm)] - x0);
+              s0 += m->D[i * P + mm] * (xe[mm + P * (j + P * k)] - x0);
+              s1 += m->D[j * P + mm] * (xe[i + P * (mm + P * k)] - y0);
+              s2 += m->D[k * P + mm] * (xe[i + P * (j + P * mm)] - z0);
             }
             A[cc][0] = s0;
             A[cc][1] = s1;

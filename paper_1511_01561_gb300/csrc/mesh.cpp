@@ -271,15 +271,16 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
       const int i = l % P, j = (l / P) % P, k = l / (P * P);
       double A[3][3];
       for (int cc = 0; cc < 3; ++cc) {
-        // element-relative coordinates: D annihilates constants, and the
-        // differences keep their precision on a 6.4e6 m shell
+        // coordinates relative to the first node of each 1D line: D
+        // annihilates constants, and the differences keep full precision even
+        // for 9e6 m wide elements on a 6.4e6 m radius shell
         const double* xc = &X[cc * Nl + b];
-        const double x0 = xc[0];
+        const double lx = xc[P * (j + P * k)], ly = xc[i + P * P * k], lz = xc[i + P * j];
         double s0 = 0, s1 = 0, s2 = 0;
         for (int q = 0; q < P; ++q) {
-          s0 += m.D[i * P + q] * (xc[q + P * (j + P * k)] - x0);
-          s1 += m.D[j * P + q] * (xc[i + P * (q + P * k)] - x0);
-          s2 += m.D[k * P + q] * (xc[i + P * (j + P * q)] - x0);
+          s0 += m.D[i * P + q] * (xc[q + P * (j + P * k)] - lx);
+          s1 += m.D[j * P + q] * (xc[i + P * (q + P * k)] - ly);
+          s2 += m.D[k * P + q] * (xc[i + P * (j + P * q)] - lz);
         }
         A[cc][0] = s0;
         A[cc][1] = s1;
