@@ -60,6 +60,20 @@ def load_peaks():
 # profiling recipe; a register-only DFMA probe on this pool measured 1.19.
 FP64_PEAK_TFLOPS = 1.25
 
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
+# source they were taken on (first 16 hex digits of its sha256).
+NCU_TRAFFIC = {"kernels_sha256_16": "06adc693a78b32a9",
+               "volume_fp64": 481.590016e6 + 141.615616e6,
+               "volume_fp32": 317.665792e6 + 133.572352e6}
+
+
+def ncu_traffic(key: str):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1511_01561_gb300", "csrc", "kernels.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return NCU_TRAFFIC.get(key) if sha == NCU_TRAFFIC["kernels_sha256_16"] else None
+
 
 def volume_flops_per_elem_node(N: int) -> float:
     """Algorithmic FP64 flops per element node of create_rhs: 39 contractions
@@ -284,7 +298,9 @@ def run_mine(args):
         "gpu_launches": 2 * nlaunch,
         "roofline": {"kernel": "volume_kernel<4,double>", "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": None, "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
+                     "traffic": ncu_traffic("volume_fp64"),
+                     "algorithmic_bytes": volume_bytes(Nl, Ng, 8),
+                     "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
                      "avg_launch_ms": 1e3 * vol_avg_s,
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},
         "kernels": {"volume_ms_avg": 1e3 * vol_avg_s, "update_ms_avg": ms_upd / nlaunch,
@@ -302,6 +318,7 @@ def run_mine(args):
             "finite": fin32,
             "roofline": {"kernel": "volume_kernel<4,float>", "bound": "hbm", "achieved": b / vol32_s / 1e9,
                          "peak": hbm_gbs, "unit": "GB/s", "frac": b / vol32_s / 1e9 / hbm_gbs,
+                         "traffic": ncu_traffic("volume_fp32"), "algorithmic_bytes": b,
                          "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
             "update_ms_avg": upd32 / nlaunch,
         }
