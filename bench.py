@@ -81,18 +81,20 @@ def volume_flops_per_elem_node(N: int) -> float:
     return 78.0 * (N + 1) + 150.0
 
 
-def volume_bytes(Nl: int, Ng: int, met_bytes: int) -> float:
-    """Algorithmic DRAM bytes of one volume-kernel launch: metric terms and
-    Jw (10 per element node), l2g (4 B), r_e write (5 FP64), and one read of
-    the gathered state and reference (8 FP64 per global node)."""
-    return Nl * (10 * met_bytes + 4 + 40) + Ng * 64
+def volume_bytes(Nl: int, Ng: int, fp: int) -> float:
+    """Algorithmic DRAM bytes of one volume-kernel launch (fp = 8 for FP64, 4
+    for the FP32-mixed form): metric terms and Jw (10 values per element node),
+    l2g (4 B), the residual write (5 values), and one read per global node of
+    the gathered fields (FP64: U and u, theta, p' = 8 doubles; FP32: 8 floats)."""
+    return Nl * (10 * fp + 4 + 5 * fp) + Ng * 8 * fp
 
 
-def update_bytes(Nl: int, Ng: int, stage_reads_qn: float) -> float:
+def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float) -> float:
     """Algorithmic DRAM bytes of one DSS/update launch: CSR (4 B per entry +
-    4 B per node), r_e read (5 FP64 per element node), M^-1, wall flag, q^k
-    read, q^{k+1} write, and q^n on the stages that use it."""
-    return Nl * (4 + 40) + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn)
+    4 B per node), residual read (5 values per element node), M^-1, wall flag,
+    q^k read, q^{k+1} write, q^n on the stages that use it, the reference
+    state (4 doubles) and the primitive-field write (40 or 32 B)."""
+    return Nl * (4 + 5 * fp) + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + (40 if fp == 8 else 32))
 
 
 class ClockSampler:
@@ -304,7 +306,7 @@ def run_mine(args):
                      "avg_launch_ms": 1e3 * vol_avg_s,
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},
         "kernels": {"volume_ms_avg": 1e3 * vol_avg_s, "update_ms_avg": ms_upd / nlaunch,
-                    "update_hbm_frac": update_bytes(Nl, Ng, 2 / 3) / (ms_upd * 1e-3 / nlaunch) / 1e9 / hbm_gbs},
+                    "update_hbm_frac": update_bytes(Nl, Ng, 8, 2 / 3) / (ms_upd * 1e-3 / nlaunch) / 1e9 / hbm_gbs},
         "clocks": ck,
         "finite": finite,
     }
@@ -321,6 +323,7 @@ def run_mine(args):
                          "traffic": ncu_traffic("volume_fp32"), "algorithmic_bytes": b,
                          "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
             "update_ms_avg": upd32 / nlaunch,
+            "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
         }
     if cpu is not None:
         line["cpu_baseline"] = cpu

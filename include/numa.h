@@ -126,17 +126,19 @@ int numa_get_state(numa_ctx* ctx, double* q, int on_device);
  * on the bound stream; returns without waiting. */
 int numa_rhs(numa_ctx* ctx, const double* q_dev, double* r_dev);
 
-/* Size of the library-owned residual scratch used by numa_rhs_static_scratch. */
+/* Size of the library-owned scratch used by numa_rhs_static_scratch. */
 #define NUMA_STATIC_SCRATCH_BYTES (16u << 20)
 
 /* The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory (code running during CUDA graph capture,
  * allocation-free real-time loops, plug-ins handed only input and output
- * buffers).  Same result as numa_rhs, but the element-residual scratch lives
- * in a fixed 16 MiB device array inside the library (NUMA_STATIC_SCRATCH_BYTES,
- * i.e. at most 419,430 element nodes) instead of the bound workspace, and
- * nothing is allocated.  Larger meshes return NUMA_EINVAL.  The first call on
- * a device looks up the array's device address; make that first call before
+ * buffers).  Same result as numa_rhs, but its scratch -- the primitive fields
+ * (40 bytes per global node) and the element residuals (40 bytes per element
+ * node in FP64, 20 in FP32-mixed) -- lives in a fixed 16 MiB device array
+ * inside the library (NUMA_STATIC_SCRATCH_BYTES; about 2,200 elements at N=4)
+ * instead of the bound workspace, and nothing is allocated.  Larger meshes
+ * return NUMA_EINVAL.  The first call on a device looks up the array's device
+ * address; make that first call before
  * any stream capture.  All calls share the array: calls that overlap on the
  * GPU race.  q_dev, r_dev: device double[5][Ng], enqueued on the bound stream. */
 int numa_rhs_static_scratch(numa_ctx* ctx, const double* q_dev, double* r_dev);

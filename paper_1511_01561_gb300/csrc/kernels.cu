@@ -1,12 +1,18 @@
 // CUDA kernels of the GB300 NUMA hot path (sm_103a):
+//   prim_kernel   : per global node, the primitive fields (u, theta, p') the
+//                   element kernel differentiates fluxes of;
 //   volume_kernel : per-element create_rhs of Eq. 4 / Eq. 5 (fluxes, tensor-
 //                   product derivatives with D, chain rule with the metric
 //                   terms, -Jw div F), one CTA per element, flux fields
 //                   staged in shared memory;
 //   update_kernel : per global node, deterministic direct stiffness
 //                   summation over a precomputed inverse map (fixed order, no
-//                   atomics), inverse mass matrix, sources, wall condition and
-//                   the SSP-RK3 stage combination.
+//                   atomics), inverse mass matrix, sources, wall condition,
+//                   the SSP-RK3 stage combination, and the primitive fields of
+//                   the new stage state.
+// GB300 executes FP64 at 1/64 of the FP32 rate, so everything that does not
+// need FP64 stays off the FP64 pipe: float<->double conversions and the
+// finiteness test are done with integer operations on the bit patterns.
 #include <cstdint>
 
 #include "numa_internal.h"
@@ -14,27 +20,107 @@
 namespace numa {
 namespace {
 
-template <typename T>
-struct Arith;
+// ---- FP64-pipe-free conversions -------------------------------------------
 
-template <>
-struct Arith<double> {
-  // p' = p0 ((1+x)^gamma - 1), x = Theta'/(rho theta)_0, without cancellation
-  static __device__ __forceinline__ double pprime(double p0, double Tp, double Th0, double gam) {
-    return p0 * expm1(gam * log1p(Tp / Th0));
-  }
-};
+// Exact float -> double.  Zero, subnormal, infinite and NaN inputs take the
+// hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
 
-template <>
-struct Arith<float> {
-  // Mixed form: the reference values stay FP64 and are combined with the
-  // state in FP64; the cancellation-free factor expm1(gamma log1p(x)) is
-  // evaluated in FP32, where it keeps full FP32 relative accuracy.
-  static __device__ __forceinline__ float pprime(double p0, double Tp, double Th0, double gam) {
-    float x = (float)(Tp / Th0);
-    return (float)p0 * expm1f((float)gam * log1pf(x));
+// double -> float, round to nearest even.  Results that are subnormal, zero,
+// infinite or NaN take the hardware conversion.
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (ex <= 0 || ex >= 255) return __double2float_rn(d);
+  // 52-bit fraction = (hi & 0xfffff) : lo; keep the top 23 bits, round on the other 29
+  const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned bits = (hi & 0x80000000u) | ((unsigned)ex << 23) | keep;
+  const unsigned half = 0x10000000u;
+  bits += (rest > half || (rest == half && (keep & 1u))) ? 1u : 0u;  // carries into the exponent
+  return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ bool nonfinite(double d) {
+  return ((((unsigned)__double2hiint(d)) >> 20) & 0x7ffu) == 0x7ffu;
+}
+
+// 1/x in FP64: FP32 seed, two Newton steps (x is a positive density).
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn(__double2float_rn(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// (1+x)^gamma - 1 with full relative accuracy: the binomial series
+// sum_k C(gamma,k) x^k (Horner) for |x| <= 1/32, else expm1(gamma log1p(x)).
+__device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
+  if (fabs(x) <= 0.03125) {
+    double t = a.eos[kEosTerms - 1];
+#pragma unroll
+    for (int k = kEosTerms - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
+    return t * x;
   }
-};
+  return expm1(a.gamma * log1p(x));
+}
+
+__device__ __forceinline__ float eos_ratio_f(float x, const PrimArgs& a) {
+  if (fabsf(x) <= 0.03125f) {
+    float t = (float)a.eos[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) t = fmaf(t, x, (float)a.eos[k]);
+    return t * x;
+  }
+  return expm1f((float)a.gamma * log1pf(x));
+}
+
+// Primitive fields of state (rp, U, Tp) at global node I (reference from a.ref):
+// rho = rho0 + rho', u = U / rho, theta = (Theta0 + Theta') / rho,
+// p' = p0 ((1 + Theta'/Theta0)^gamma - 1).
+__device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, double rp, double Ux, double Uy,
+                                           double Uz, double Tp) {
+  const long long Ng = a.Ng;
+  const double rho0 = a.ref[I], Th0 = a.ref[Ng + I], p0 = a.ref[2 * Ng + I], iTh0 = a.ref[3 * Ng + I];
+  const double rho = rho0 + rp;
+  const double Th = Th0 + Tp;
+  if (a.precision == NUMA_FP32_MIXED) {
+    // reference + perturbation in FP64, the rest in FP32
+    float* w = static_cast<float*>(a.prim);
+    const float rf = 1.0f / d2f(rho);
+    const float Uxf = d2f(Ux), Uyf = d2f(Uy), Uzf = d2f(Uz);
+    w[I] = Uxf;
+    w[Ng + I] = Uyf;
+    w[2 * Ng + I] = Uzf;
+    w[3 * Ng + I] = Uxf * rf;
+    w[4 * Ng + I] = Uyf * rf;
+    w[5 * Ng + I] = Uzf * rf;
+    w[6 * Ng + I] = d2f(Th) * rf;
+    w[7 * Ng + I] = d2f(p0) * eos_ratio_f(d2f(Tp) * d2f(iTh0), a);
+  } else {
+    double* w = static_cast<double*>(a.prim);
+    const double r = rcp64(rho);
+    w[I] = Ux * r;
+    w[Ng + I] = Uy * r;
+    w[2 * Ng + I] = Uz * r;
+    w[3 * Ng + I] = Th * r;
+    w[4 * Ng + I] = p0 * eos_ratio(Tp * iTh0, a);
+  }
+}
+
+__global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
+  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= a.Ng) return;
+  const long long Ng = a.Ng;
+  write_prim(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
+}
 
 // Field slots of the 13 unique flux components staged per element node.
 enum : int { kUx = 0, kUy, kUz, kTxx, kTxy, kTxz, kTyy, kTyz, kTzz, kPp, kHx, kHy, kHz, kNF };
@@ -61,32 +147,44 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
   const long long n = (long long)e * NP + l;
   const long long Ng = a.Ng, Nl = a.Nl;
   if (l < NP) {
-    // primitive variables at this element node (the state is FP64)
+    // gather this node's momentum and primitive fields (CG storage)
     const int g = a.l2g[n];
-    const double rp = a.q[g];
-    const double Ux = a.q[Ng + g], Uy = a.q[2 * Ng + g], Uz = a.q[3 * Ng + g];
-    const double Tp = a.q[4 * Ng + g];
-    const double rho0 = a.ref[g], Th0 = a.ref[Ng + g], p0 = a.ref[2 * Ng + g];
-    const double rho = rho0 + rp;
-    const double Th = Th0 + Tp;
-    const T pp = Arith<T>::pprime(p0, Tp, Th0, a.gamma);
-    const T rinv = T(1) / T(rho);
-    const T ux = T(Ux) * rinv, uy = T(Uy) * rinv, uz = T(Uz) * rinv;
-    const T th = T(Th) * rinv;
+    T Ux, Uy, Uz, ux, uy, uz, th, pp;
+    if constexpr (sizeof(T) == 8) {
+      const double* w = static_cast<const double*>(a.prim);
+      Ux = a.q[Ng + g];
+      Uy = a.q[2 * Ng + g];
+      Uz = a.q[3 * Ng + g];
+      ux = w[g];
+      uy = w[Ng + g];
+      uz = w[2 * Ng + g];
+      th = w[3 * Ng + g];
+      pp = w[4 * Ng + g];
+    } else {
+      const float* w = static_cast<const float*>(a.prim);
+      Ux = w[g];
+      Uy = w[Ng + g];
+      Uz = w[2 * Ng + g];
+      ux = w[3 * Ng + g];
+      uy = w[4 * Ng + g];
+      uz = w[5 * Ng + g];
+      th = w[6 * Ng + g];
+      pp = w[7 * Ng + g];
+    }
     // F_rho = U, F_U = U (x) u + p' I (symmetric part stored once), F_Theta = theta U
-    F[kUx * NP + l] = T(Ux);
-    F[kUy * NP + l] = T(Uy);
-    F[kUz * NP + l] = T(Uz);
-    F[kTxx * NP + l] = T(Ux) * ux;
-    F[kTxy * NP + l] = T(Ux) * uy;
-    F[kTxz * NP + l] = T(Ux) * uz;
-    F[kTyy * NP + l] = T(Uy) * uy;
-    F[kTyz * NP + l] = T(Uy) * uz;
-    F[kTzz * NP + l] = T(Uz) * uz;
+    F[kUx * NP + l] = Ux;
+    F[kUy * NP + l] = Uy;
+    F[kUz * NP + l] = Uz;
+    F[kTxx * NP + l] = Ux * ux;
+    F[kTxy * NP + l] = Ux * uy;
+    F[kTxz * NP + l] = Ux * uz;
+    F[kTyy * NP + l] = Uy * uy;
+    F[kTyz * NP + l] = Uy * uz;
+    F[kTzz * NP + l] = Uz * uz;
     F[kPp * NP + l] = pp;
-    F[kHx * NP + l] = th * T(Ux);
-    F[kHy * NP + l] = th * T(Uy);
-    F[kHz * NP + l] = th * T(Uz);
+    F[kHx * NP + l] = th * Ux;
+    F[kHy * NP + l] = th * Uy;
+    F[kHz * NP + l] = th * Uz;
   }
   __syncthreads();
   if (l >= NP) return;
@@ -136,28 +234,35 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
   dref(kHy, s0, s1, s2); div_t += phys(1, s0, s1, s2);
   dref(kHz, s0, s1, s2); div_t += phys(2, s0, s1, s2);
   // element residual -Jw div F (Eq. 4); the sources are added per global node
-  a.re[n] = -(double)(jw * div_r);
-  a.re[Nl + n] = -(double)(jw * div_x);
-  a.re[2 * Nl + n] = -(double)(jw * div_y);
-  a.re[3 * Nl + n] = -(double)(jw * div_z);
-  a.re[4 * Nl + n] = -(double)(jw * div_t);
+  T* re = static_cast<T*>(a.re);
+  re[n] = -(jw * div_r);
+  re[Nl + n] = -(jw * div_x);
+  re[2 * Nl + n] = -(jw * div_y);
+  re[3 * Nl + n] = -(jw * div_z);
+  re[4 * Nl + n] = -(jw * div_t);
 }
 
-template <int MODE, bool SHELL>
+template <typename RT>
+__device__ __forceinline__ double re_load(const void* re, long long idx) {
+  if constexpr (sizeof(RT) == 8) return static_cast<const double*>(re)[idx];
+  else return f2d(static_cast<const float*>(re)[idx]);
+}
+
+template <int MODE, bool SHELL, typename RT>
 __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
   const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= a.Ng) return;
   const long long Ng = a.Ng, Nl = a.Nl;
-  // direct stiffness summation in ascending element-node order (Eq. 4)
+  // direct stiffness summation in ascending element-node order (Eq. 4), FP64
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
   const int t0 = a.off[I], t1 = a.off[I + 1];
   for (int t = t0; t < t1; ++t) {
     const long long n = a.idx[t];
-    s0 += a.re[n];
-    s1 += a.re[Nl + n];
-    s2 += a.re[2 * Nl + n];
-    s3 += a.re[3 * Nl + n];
-    s4 += a.re[4 * Nl + n];
+    s0 += re_load<RT>(a.re, n);
+    s1 += re_load<RT>(a.re, Nl + n);
+    s2 += re_load<RT>(a.re, 2 * Nl + n);
+    s3 += re_load<RT>(a.re, 3 * Nl + n);
+    s4 += re_load<RT>(a.re, 4 * Nl + n);
   }
   const double minv = a.Minv[I];
   double R0 = s0 * minv, R1 = s1 * minv, R2 = s2 * minv, R3 = s3 * minv, R4 = s4 * minv;
@@ -192,20 +297,18 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
     const double bdt = a.b * a.dt;
     double y[5];
     const double R[5] = {R0, R1, R2, R3, R4};
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const double qk = a.qk[v * Ng + I];
-      double t = fma(a.b, qk, bdt * R[v]);
-      if (a.a != 0.0) t = fma(a.a, a.qn[v * Ng + I], t);
-      y[v] = t;
-    }
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      a.out[v * Ng + I] = y[v];
-      bad |= !isfinite(y[v]);
+      const double qk = (v == 0) ? rp : a.qk[v * Ng + I];
+      double t = fma(a.b, qk, bdt * R[v]);
+      if (a.a != 0.0) t = fma(a.a, a.qn[v * Ng + I], t);
+      y[v] = t;
+      a.out[v * Ng + I] = t;
+      bad |= nonfinite(t);
     }
     if (bad) atomicOr(a.flag, 1);
+    write_prim(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
   }
 }
 
@@ -240,24 +343,37 @@ cudaError_t launch_volume_p(int N, const VolumeArgs& a, cudaStream_t s) {
   }
 }
 
+template <int MODE, typename RT>
+void launch_update_m(const UpdateArgs& a, unsigned nb, int nt, cudaStream_t s) {
+  if (a.gvec) update_kernel<MODE, true, RT><<<nb, nt, 0, s>>>(a);
+  else update_kernel<MODE, false, RT><<<nb, nt, 0, s>>>(a);
+}
+
 }  // namespace
+
+cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
+  if (a.Ng == 0) return cudaSuccess;
+  const int nt = 256;
+  prim_kernel<<<(unsigned)((a.Ng + nt - 1) / nt), nt, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
   if (precision == NUMA_FP32_MIXED) return launch_volume_p<float>(N, a, s);
   return launch_volume_p<double>(N, a, s);
 }
 
-cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
+cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   if (a.Ng == 0) return cudaSuccess;
   const int nt = 256;
   const unsigned nb = (unsigned)((a.Ng + nt - 1) / nt);
-  const bool shell = a.gvec != nullptr;
+  const bool f32 = precision == NUMA_FP32_MIXED;
   if (a.mode == 0) {
-    if (shell) update_kernel<0, true><<<nb, nt, 0, s>>>(a);
-    else update_kernel<0, false><<<nb, nt, 0, s>>>(a);
+    if (f32) launch_update_m<0, float>(a, nb, nt, s);
+    else launch_update_m<0, double>(a, nb, nt, s);
   } else {
-    if (shell) update_kernel<1, true><<<nb, nt, 0, s>>>(a);
-    else update_kernel<1, false><<<nb, nt, 0, s>>>(a);
+    if (f32) launch_update_m<1, float>(a, nb, nt, s);
+    else launch_update_m<1, double>(a, nb, nt, s);
   }
   return cudaGetLastError();
 }

@@ -327,7 +327,7 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
   }
   // hydrostatic reference state from the geopotential Phi (g z in the box,
   // g0 a (1 - a/r) on the shell) and, on the shell, the gravity vectors
-  m.ref.assign(3 * Ng, 0.0);
+  m.ref.assign(4 * Ng, 0.0);
   if (c.mesh_kind == NUMA_MESH_SHELL) {
     m.gvec.assign(3 * Ng, 0.0);
     m.nrm.assign(3 * Ng, 0.0);
@@ -370,6 +370,7 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
     m.ref[g] = rho0;
     m.ref[Ng + g] = Th0;
     m.ref[2 * Ng + g] = p0;
+    m.ref[3 * Ng + g] = 1.0 / Th0;
   }
   return true;
 }

@@ -1,6 +1,6 @@
-// numa_rhs_static_scratch: the right-hand side with its element-residual
-// scratch in a fixed, library-owned device array instead of the caller's
-// workspace.
+// numa_rhs_static_scratch: the right-hand side with its scratch (primitive
+// fields and element residuals) in a fixed, library-owned device array
+// instead of the caller's workspace.
 //
 // Who needs this: callers that cannot allocate device memory themselves --
 // code that runs while a CUDA graph is being captured, real-time loops that
@@ -11,12 +11,13 @@
 // point evaluates R = dq/dt on the caller's own buffers with a scratch array
 // that is part of the library image: nothing is allocated per call.
 //
-// The array is 16 MiB (5 doubles per element node, so at most 419,430
-// element nodes).  Every GPU that loads this library keeps it until the
+// The array is 16 MiB: 40 bytes per global node of primitive fields plus 40
+// (FP64) or 20 (FP32-mixed) bytes per element node of residuals, about 2,200
+// elements at N=4.  Every GPU that loads this library keeps it until the
 // process exits.  All calls share it: two calls whose work overlaps on the
 // GPU (different streams, or different contexts) race on it.  Nothing in it
-// needs clearing between calls, because the volume kernel overwrites every
-// entry the summation kernel then reads.
+// needs clearing between calls: each call overwrites every primitive and
+// residual entry before the next kernel reads it.
 #include <mutex>
 #include <string>
 

@@ -17,9 +17,11 @@ struct numa_ctx {
   HostMesh mesh;
   DevLayout L;
   bool bound = false;
+  bool prim_valid = false;  // L.prim holds the primitive fields of L.q
   cudaStream_t stream = nullptr;
   std::string err;
   double gamma = 1.4;
+  double eos[kEosTerms];
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   double graph_dt = NAN;
@@ -45,29 +47,40 @@ int cuda_fail(numa_ctx* c, cudaError_t e, const char* what) {
 const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0};
 const double kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
 
-VolumeArgs volume_args(const numa_ctx* c, const double* q) {
-  VolumeArgs a;
+PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim) {
+  PrimArgs a;
   a.q = q;
   a.ref = c->L.ref;
+  a.prim = prim;
+  a.Ng = c->mesh.Ng;
+  a.precision = c->cfg.precision;
+  a.gamma = c->gamma;
+  for (int k = 0; k < kEosTerms; ++k) a.eos[k] = c->eos[k];
+  return a;
+}
+
+VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, void* re) {
+  VolumeArgs a;
+  a.q = q;
+  a.prim = prim;
   a.l2g = c->L.l2g;
   a.met64 = c->L.met64;
   a.met32 = c->L.met32;
   a.D64 = c->L.D64;
   a.D32 = c->L.D32;
-  a.re = c->L.re;
+  a.re = re;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
-  a.gamma = c->gamma;
   return a;
 }
 
-UpdateArgs update_args(const numa_ctx* c, const double* qk, const double* qn, double* out, int mode, double ra,
-                       double rb, double dt) {
+UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, const double* qn, double* out,
+                       int mode, double ra, double rb, double dt) {
   UpdateArgs a;
   a.off = c->L.csr_off;
   a.idx = c->L.csr_idx;
-  a.re = c->L.re;
+  a.re = re;
   a.Minv = c->L.Minv;
   a.wall = c->L.wall;
   a.gvec = c->L.gvec;
@@ -84,19 +97,45 @@ UpdateArgs update_args(const numa_ctx* c, const double* qk, const double* qn, do
   a.dt = dt;
   a.mode = mode;
   a.flag = c->L.flags;
+  a.pa = prim_args(c, nullptr, c->L.prim);
   return a;
 }
 
-// One SSP-RK3 step on stream s: three times (create_rhs; DSS + M^-1 + update q).
-cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s) {
+// R(q) into r_dev with the given primitive and residual scratch.
+cudaError_t enqueue_rhs(numa_ctx* c, const double* q, double* r, void* prim, void* re) {
+  cudaError_t e = launch_prim(prim_args(c, q, prim), c->stream);
+  if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, q, prim, re), c->stream);
+  if (e == cudaSuccess) e = launch_update(c->cfg.precision, update_args(c, re, q, q, r, 0, 0.0, 1.0, 0.0), c->stream);
+  return e;
+}
+
+// Primitive fields of the current state, if the state changed since they were made.
+cudaError_t ensure_prim(numa_ctx* c) {
+  if (c->prim_valid) return cudaSuccess;
+  cudaError_t e = launch_prim(prim_args(c, c->L.q, c->L.prim), c->stream);
+  if (e == cudaSuccess) c->prim_valid = true;
+  return e;
+}
+
+// One SSP-RK3 step on stream s: three times (create_rhs; DSS + M^-1 + update
+// q, which also leaves the primitive fields of the new stage state).  Needs
+// the primitive fields of q^n on entry and leaves those of q^{n+1}.
+// With ev != nullptr every kernel is bracketed by events (12 per step).
+cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   double* q = c->L.q;
   double* qs = c->L.qs;
   const double* qin[3] = {q, qs, qs};
   double* qout[3] = {qs, qs, q};
   for (int st = 0; st < 3; ++st) {
-    cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st]), s);
-    if (e != cudaSuccess) return e;
-    e = launch_update(update_args(c, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt), s);
+    cudaError_t e = ev ? cudaEventRecord(ev[4 * st], s) : cudaSuccess;
+    if (e == cudaSuccess)
+      e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st], c->L.prim, c->L.re), s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 1], s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 2], s);
+    if (e == cudaSuccess)
+      e = launch_update(c->cfg.precision, update_args(c, c->L.re, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt),
+                        s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 3], s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -105,6 +144,10 @@ cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s) {
 }  // namespace
 
 namespace numa {
+
+size_t residual_bytes(const numa_config& c, const HostMesh& m) {
+  return 5 * (size_t)m.Nl * (c.precision == NUMA_FP32_MIXED ? 4 : 8);
+}
 
 size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, DevLayout* L) {
   size_t off = 0;
@@ -118,13 +161,14 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.flags = (int*)take(64 * sizeof(int));
   d.q = (double*)take(5 * Ng * 8);
   d.qs = (double*)take(5 * Ng * 8);
-  d.re = (double*)take(5 * Nl * 8);
+  d.prim = take(kPrimBytesPerNode * Ng);
+  d.re = take(residual_bytes(c, m));
   if (c.precision == NUMA_FP32_MIXED) d.met32 = (float*)take(10 * Nl * 4);
   else d.met64 = (double*)take(10 * Nl * 8);
   d.l2g = (int32_t*)take(Nl * 4);
   d.csr_off = (int32_t*)take((Ng + 1) * 4);
   d.csr_idx = (int32_t*)take(Nl * 4);
-  d.ref = (double*)take(3 * Ng * 8);
+  d.ref = (double*)take(4 * Ng * 8);
   d.Minv = (double*)take(Ng * 8);
   d.wall = (uint8_t*)take(Ng);
   if (c.mesh_kind == NUMA_MESH_SHELL) {
@@ -138,22 +182,21 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   return off;
 }
 
-// RHS with a caller-chosen residual scratch (used by numa_rhs_static_scratch).
-int rhs_with_scratch(numa_ctx* c, const double* q_dev, double* r_dev, double* re_scratch,
-                     long long scratch_doubles) {
-  if (!c || !q_dev || !r_dev || !re_scratch) return NUMA_EINVAL;
+// RHS with caller-chosen scratch for the primitive fields and the element
+// residuals (used by numa_rhs_static_scratch): the scratch holds
+// kPrimBytesPerNode * Ng bytes of primitives, 256-byte aligned, then the
+// residuals.
+int rhs_with_scratch(numa_ctx* c, const double* q_dev, double* r_dev, double* scratch, long long scratch_doubles) {
+  if (!c || !q_dev || !r_dev || !scratch) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rhs_static_scratch before numa_bind");
   if ((const void*)q_dev == (const void*)r_dev) return fail(c, NUMA_EINVAL, "q and r must not alias");
-  if (5 * c->mesh.Nl > scratch_doubles)
-    return fail(c, NUMA_EINVAL, "mesh needs " + std::to_string(40 * c->mesh.Nl) +
-                                    " bytes of residual scratch; the static array holds " +
+  const size_t prim_bytes = align_up(kPrimBytesPerNode * (size_t)c->mesh.Ng);
+  const size_t need = prim_bytes + residual_bytes(c->cfg, c->mesh);
+  if (need > 8 * (size_t)scratch_doubles)
+    return fail(c, NUMA_EINVAL, "mesh needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
                                     std::to_string(8 * scratch_doubles));
-  VolumeArgs va = volume_args(c, q_dev);
-  va.re = re_scratch;
-  UpdateArgs ua = update_args(c, q_dev, q_dev, r_dev, 0, 0.0, 1.0, 0.0);
-  ua.re = re_scratch;
-  cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, va, c->stream);
-  if (e == cudaSuccess) e = launch_update(ua, c->stream);
+  char* base = reinterpret_cast<char*>(scratch);
+  cudaError_t e = enqueue_rhs(c, q_dev, r_dev, base, base + prim_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_rhs_static_scratch launch");
   return NUMA_OK;
 }
@@ -172,6 +215,12 @@ int numa_create(const numa_config* cfg, numa_ctx** out) {
   if (!c) return NUMA_ENOMEM;
   c->cfg = *cfg;
   c->gamma = cfg->cp / cfg->cv;
+  // binomial coefficients C(gamma, k) of (1+x)^gamma - 1 = sum_k C(gamma,k) x^k
+  double ck = 1.0;
+  for (int k = 1; k <= kEosTerms; ++k) {
+    ck *= (c->gamma - (k - 1)) / k;
+    c->eos[k - 1] = ck;
+  }
   try {
     if (!build_host_mesh(c->cfg, c->mesh, c->err)) {
       delete c;
@@ -225,7 +274,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
   up(L.csr_idx, m.csr_idx.data(), Nl * 4);
-  up(L.ref, m.ref.data(), 3 * Ng * 8);
+  up(L.ref, m.ref.data(), 4 * Ng * 8);
   up(L.Minv, m.Minv.data(), Ng * 8);
   up(L.wall, m.wall.data(), Ng);
   if (L.gvec) up(L.gvec, m.gvec.data(), 3 * Ng * 8);
@@ -235,14 +284,15 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(L.qs, 0, 5 * Ng * 8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind upload");
+  c->L = L;
   // kernel attributes are set outside any stream capture
-  VolumeArgs probe = volume_args(c, L.q);
+  VolumeArgs probe = volume_args(c, L.q, L.prim, L.re);
   probe.Ne = 0;
   e = launch_volume(m.N, c->cfg.precision, probe, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind kernel setup");
-  c->L = L;
   c->stream = s;
   c->bound = true;
+  c->prim_valid = false;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -261,6 +311,7 @@ int numa_init_state(numa_ctx* c, int kind, const double* params, int nparams) {
     return fail(c, NUMA_ENOMEM, "host allocation");
   }
   if (!init_state_host(c->cfg, c->mesh, kind, params, nparams, q.data(), c->err)) return NUMA_EINVAL;
+  c->prim_valid = false;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q.data(), q.size() * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_init_state upload");
@@ -270,6 +321,7 @@ int numa_init_state(numa_ctx* c, int kind, const double* params, int nparams) {
 int numa_set_state(numa_ctx* c, const double* q, int on_device) {
   if (!c || !q) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_set_state before numa_bind");
+  c->prim_valid = false;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
@@ -291,8 +343,8 @@ int numa_rhs(numa_ctx* c, const double* q_dev, double* r_dev) {
   if (!c || !q_dev || !r_dev) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rhs before numa_bind");
   if ((const void*)q_dev == (const void*)r_dev) return fail(c, NUMA_EINVAL, "q and r must not alias");
-  cudaError_t e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, q_dev), c->stream);
-  if (e == cudaSuccess) e = launch_update(update_args(c, q_dev, q_dev, r_dev, 0, 0.0, 1.0, 0.0), c->stream);
+  c->prim_valid = false;  // the primitive scratch now describes q_dev
+  cudaError_t e = enqueue_rhs(c, q_dev, r_dev, c->L.prim, c->L.re);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_rhs launch");
   return NUMA_OK;
 }
@@ -301,7 +353,8 @@ int numa_rk_step(numa_ctx* c, double dt) {
   if (!c) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rk_step before numa_bind");
   if (!std::isfinite(dt)) return fail(c, NUMA_EINVAL, "dt must be finite");
-  cudaError_t e = enqueue_rk_step(c, dt, c->stream);
+  cudaError_t e = ensure_prim(c);
+  if (e == cudaSuccess) e = enqueue_rk_step(c, dt, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_rk_step launch");
   return NUMA_OK;
 }
@@ -330,6 +383,7 @@ int numa_run(numa_ctx* c, double dt, int nsteps) {
     c->graph_dt = dt;
     c->graph_q = c->L.q;
   }
+  if (nsteps > 0) e = ensure_prim(c);
   for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = cudaGraphLaunch(c->graph, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_run graph launch");
   int flag = 0;
@@ -343,32 +397,17 @@ int numa_time_kernels(numa_ctx* c, double dt, int nsteps, double* ms_volume, dou
   if (!c || !ms_volume || !ms_update) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_time_kernels before numa_bind");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NUMA_EINVAL, "bad nsteps or dt");
-  const int nk = 3 * nsteps;
-  std::vector<cudaEvent_t> ev(4 * (size_t)nk, nullptr);
-  cudaError_t e = cudaSuccess;
+  std::vector<cudaEvent_t> ev(12 * (size_t)nsteps, nullptr);
+  cudaError_t e = ensure_prim(c);
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
-  double* q = c->L.q;
-  double* qs = c->L.qs;
-  const double* qin[3] = {q, qs, qs};
-  double* qout[3] = {qs, qs, q};
-  for (int t = 0; t < nk && e == cudaSuccess; ++t) {
-    const int st = t % 3;
-    cudaEvent_t* E = &ev[4 * (size_t)t];
-    e = cudaEventRecord(E[0], c->stream);
-    if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st]), c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(E[1], c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(E[2], c->stream);
-    if (e == cudaSuccess)
-      e = launch_update(update_args(c, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt), c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(E[3], c->stream);
-  }
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = enqueue_rk_step(c, dt, c->stream, &ev[12 * (size_t)t]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   double tv = 0.0, tu = 0.0;
-  for (int t = 0; t < nk && e == cudaSuccess; ++t) {
+  for (size_t t = 0; t < 3 * (size_t)nsteps && e == cudaSuccess; ++t) {
     float a = 0.f, b = 0.f;
-    e = cudaEventElapsedTime(&a, ev[4 * (size_t)t], ev[4 * (size_t)t + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * (size_t)t + 2], ev[4 * (size_t)t + 3]);
+    e = cudaEventElapsedTime(&a, ev[4 * t], ev[4 * t + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * t + 2], ev[4 * t + 3]);
     tv += a;
     tu += b;
   }

@@ -13,6 +13,7 @@
 namespace numa {
 
 constexpr int kMaxN = 8;
+constexpr int kEosTerms = 12;  // binomial-series terms of (1+x)^gamma - 1 for |x| <= 1/32
 
 // Host-side mesh and geometry (Sec. 2.1: Lobatto points, Eq. 4: Jw and M,
 // Eq. 5: isoparametric metric terms).  Built once per context.
@@ -25,7 +26,7 @@ struct HostMesh {
   std::vector<int32_t> csr_off;       // global node -> first entry in csr_idx [Ng+1]
   std::vector<int32_t> csr_idx;       // element nodes of each global node, ascending [Nl]
   std::vector<double> met;            // [10][Nl]: dxi_d/dx_c at row 3d+c, then Jw
-  std::vector<double> ref;            // [3][Ng]: rho0, (rho theta)_0, p0
+  std::vector<double> ref;            // [4][Ng]: rho0, (rho theta)_0, p0, 1/(rho theta)_0
   std::vector<double> Minv;           // [Ng]: 1 / sum_e Jw
   std::vector<uint8_t> wall;          // [Ng]: bit a = box wall normal to axis a; bit 3 = shell radial wall
   std::vector<double> gvec;           // shell only, [3][Ng]: g(r) r_hat
@@ -37,17 +38,25 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err);
 bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const double* prm, int nprm,
                      double* q, std::string& err);
 
+// Per-global-node primitive fields that the volume kernel gathers, written by
+// the stage update (or the primitive pass) for the state the next create_rhs
+// differentiates:
+//   FP64 mode : double [5][Ng] = u_x, u_y, u_z, theta, p'   (U comes from q)
+//   FP32 mode : float  [8][Ng] = U_x, U_y, U_z, u_x, u_y, u_z, theta, p'
+constexpr int kPrimBytesPerNode = 40;
+
 // Device workspace carved from the caller's buffer.
 struct DevLayout {
   double* q = nullptr;       // state q^n [5][Ng]
   double* qs = nullptr;      // stage state [5][Ng]
-  double* re = nullptr;      // element-local residuals -Jw div F [5][Nl] (scratch)
+  void* prim = nullptr;      // primitive fields (scratch) [kPrimBytesPerNode * Ng]
+  void* re = nullptr;        // element residuals -Jw div F (scratch): double or float [5][Nl]
   double* met64 = nullptr;   // [10][Nl] FP64 metric terms and Jw
   float* met32 = nullptr;    // [10][Nl] FP32 copy (mixed-precision form)
   int32_t* l2g = nullptr;
   int32_t* csr_off = nullptr;
   int32_t* csr_idx = nullptr;
-  double* ref = nullptr;     // [3][Ng]
+  double* ref = nullptr;     // [4][Ng]
   double* Minv = nullptr;    // [Ng]
   uint8_t* wall = nullptr;   // [Ng]
   double* gvec = nullptr;    // [3][Ng] (shell)
@@ -59,27 +68,37 @@ struct DevLayout {
 };
 
 size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, DevLayout* L);
+size_t residual_bytes(const numa_config& c, const HostMesh& m);  // bytes of the re scratch
 
 // ---- kernels -------------------------------------------------------------
 
+struct PrimArgs {
+  const double* q;     // state the primitives describe [5][Ng]
+  const double* ref;   // [4][Ng]
+  void* prim;          // output
+  long long Ng;
+  int precision;
+  double gamma;
+  double eos[kEosTerms];  // binomial coefficients C(gamma, k), k = 1..kEosTerms
+};
+
 struct VolumeArgs {
-  const double* q;    // state [5][Ng]
-  const double* ref;  // [3][Ng]
+  const double* q;     // state [5][Ng] (FP64 mode reads U from it)
+  const void* prim;    // primitive fields of q
   const int32_t* l2g;
   const double* met64;
   const float* met32;
   const double* D64;
   const float* D32;
-  double* re;         // [5][Nl]
+  void* re;            // [5][Nl] output
   long long Ng, Nl;
   int Ne;
-  double gamma;
 };
 
 struct UpdateArgs {
   const int32_t* off;
   const int32_t* idx;
-  const double* re;
+  const void* re;
   const double* Minv;
   const uint8_t* wall;
   const double* gvec;  // shell gravity vectors or null (box)
@@ -91,11 +110,13 @@ struct UpdateArgs {
   double g;            // box gravity
   double two_omega;    // shell Coriolis 2 Omega
   double a, b, dt;     // out = a qn + b (qk + dt R)
-  int mode;            // 0: write R, 1: RK stage
+  int mode;            // 0: write R, 1: RK stage (also writes the primitives of out)
   int* flag;           // non-finite flag
+  PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
 };
 
+cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s);
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s);
-cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 
 }  // namespace numa

@@ -1,8 +1,9 @@
 """numa_rhs_static_scratch: the right-hand side for callers that cannot
 allocate device memory (graph capture, allocation-free loops, plug-ins that
-are handed only input and output buffers).  Its element-residual scratch is
-a fixed 16 MiB array inside the library, so it must give the same result as
-numa_rhs, call after call, and refuse meshes that do not fit.
+are handed only input and output buffers).  Its scratch (primitive fields
+and element residuals) is a fixed 16 MiB array inside the library, so it
+must give the same result as numa_rhs, call after call, and refuse meshes
+that do not fit.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
