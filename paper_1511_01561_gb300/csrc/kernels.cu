@@ -22,20 +22,22 @@ namespace {
 
 // ---- FP64-pipe-free conversions -------------------------------------------
 
-// Exact float -> double.  Zero, subnormal, infinite and NaN inputs take the
-// hardware conversion.
+// Exact float -> double.  Subnormal, infinite and NaN inputs take the
+// hardware conversion (zeros, common in a state at rest, do not).
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
   if (ex == 0u || ex == 0xffu) return (double)f;
   const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// double -> float, round to nearest even.  Results that are subnormal, zero,
-// infinite or NaN take the hardware conversion.
+// double -> float, round to nearest even.  Results that are subnormal,
+// infinite or NaN take the hardware conversion; zeros do not.
 __device__ __forceinline__ float d2f(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);
   const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
   if (ex <= 0 || ex >= 255) return __double2float_rn(d);
   // 52-bit fraction = (hi & 0xfffff) : lo; keep the top 23 bits, round on the other 29
@@ -51,9 +53,10 @@ __device__ __forceinline__ bool nonfinite(double d) {
   return ((((unsigned)__double2hiint(d)) >> 20) & 0x7ffu) == 0x7ffu;
 }
 
-// 1/x in FP64: FP32 seed, two Newton steps (x is a positive density).
+// 1/x in FP64 for a positive density: FP32 reciprocal seed (conversions by
+// integer ops), two Newton steps.
 __device__ __forceinline__ double rcp64(double x) {
-  double r = (double)__frcp_rn(__double2float_rn(x));
+  double r = f2d(__frcp_rn(d2f(x)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
@@ -61,9 +64,18 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 // (1+x)^gamma - 1 with full relative accuracy: the binomial series
-// sum_k C(gamma,k) x^k (Horner) for |x| <= 1/32, else expm1(gamma log1p(x)).
+// sum_k C(gamma,k) x^k (Horner), 6 terms for |x| <= 2^-10 and 12 terms for
+// |x| <= 2^-5 (truncation below 1e-17 relative in both), else
+// expm1(gamma log1p(x)).
 __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
-  if (fabs(x) <= 0.03125) {
+  const double ax = fabs(x);
+  if (ax <= 0.0009765625) {
+    double t = a.eos[5];
+#pragma unroll
+    for (int k = 4; k >= 0; --k) t = fma(t, x, a.eos[k]);
+    return t * x;
+  }
+  if (ax <= 0.03125) {
     double t = a.eos[kEosTerms - 1];
 #pragma unroll
     for (int k = kEosTerms - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
@@ -253,10 +265,13 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
   const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= a.Ng) return;
   const long long Ng = a.Ng, Nl = a.Nl;
-  // direct stiffness summation in ascending element-node order (Eq. 4), FP64
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+  // direct stiffness summation in ascending element-node order (Eq. 4), FP64;
+  // every global node has at least one element node
   const int t0 = a.off[I], t1 = a.off[I + 1];
-  for (int t = t0; t < t1; ++t) {
+  const long long n0 = a.idx[t0];
+  double s0 = re_load<RT>(a.re, n0), s1 = re_load<RT>(a.re, Nl + n0), s2 = re_load<RT>(a.re, 2 * Nl + n0);
+  double s3 = re_load<RT>(a.re, 3 * Nl + n0), s4 = re_load<RT>(a.re, 4 * Nl + n0);
+  for (int t = t0 + 1; t < t1; ++t) {
     const long long n = a.idx[t];
     s0 += re_load<RT>(a.re, n);
     s1 += re_load<RT>(a.re, Nl + n);
@@ -265,47 +280,66 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
     s4 += re_load<RT>(a.re, 4 * Nl + n);
   }
   const double minv = a.Minv[I];
-  double R0 = s0 * minv, R1 = s1 * minv, R2 = s2 * minv, R3 = s3 * minv, R4 = s4 * minv;
-  // sources at the global node: buoyancy of rho' (and Coriolis on the shell)
   const double rp = a.qk[I];
   const uint8_t w = a.wall[I];
-  if constexpr (SHELL) {
-    const double gx = a.gvec[I], gy = a.gvec[Ng + I], gz = a.gvec[2 * Ng + I];
-    R1 = fma(-rp, gx, R1) + a.two_omega * a.qk[2 * Ng + I];
-    R2 = fma(-rp, gy, R2) - a.two_omega * a.qk[Ng + I];
-    R3 = fma(-rp, gz, R3);
-    if (w & 8) {  // remove the radial momentum tendency at the bottom and lid
-      const double nx = a.nrm[I], ny = a.nrm[Ng + I], nz = a.nrm[2 * Ng + I];
-      const double dot = R1 * nx + R2 * ny + R3 * nz;
-      R1 -= dot * nx;
-      R2 -= dot * ny;
-      R3 -= dot * nz;
+  if constexpr (MODE == 0 || SHELL) {
+    // R = M^-1 DSS(r_e) + S, then the wall condition
+    double R0 = s0 * minv, R1 = s1 * minv, R2 = s2 * minv, R3 = s3 * minv, R4 = s4 * minv;
+    if constexpr (SHELL) {
+      // buoyancy of rho' along g(r) r_hat and Coriolis -2 Omega z x U
+      const double gx = a.gvec[I], gy = a.gvec[Ng + I], gz = a.gvec[2 * Ng + I];
+      R1 = fma(-rp, gx, R1) + a.two_omega * a.qk[2 * Ng + I];
+      R2 = fma(-rp, gy, R2) - a.two_omega * a.qk[Ng + I];
+      R3 = fma(-rp, gz, R3);
+      if (w & 8) {  // remove the radial momentum tendency at the bottom and lid
+        const double nx = a.nrm[I], ny = a.nrm[Ng + I], nz = a.nrm[2 * Ng + I];
+        const double dot = R1 * nx + R2 * ny + R3 * nz;
+        R1 -= dot * nx;
+        R2 -= dot * ny;
+        R3 -= dot * nz;
+      }
+    } else {
+      R3 = fma(-rp, a.g, R3);
+      if (w & 1) R1 = 0.0;
+      if (w & 2) R2 = 0.0;
+      if (w & 4) R3 = 0.0;
     }
-  } else {
-    R3 = fma(-rp, a.g, R3);
-    if (w & 1) R1 = 0.0;
-    if (w & 2) R2 = 0.0;
-    if (w & 4) R3 = 0.0;
+    if constexpr (MODE == 0) {
+      a.out[I] = R0;
+      a.out[Ng + I] = R1;
+      a.out[2 * Ng + I] = R2;
+      a.out[3 * Ng + I] = R3;
+      a.out[4 * Ng + I] = R4;
+      return;
+    }
+    s0 = R0;  // the stage combination below takes the full tendency
+    s1 = R1;
+    s2 = R2;
+    s3 = R3;
+    s4 = R4;
   }
-  if constexpr (MODE == 0) {
-    a.out[I] = R0;
-    a.out[Ng + I] = R1;
-    a.out[2 * Ng + I] = R2;
-    a.out[3 * Ng + I] = R3;
-    a.out[4 * Ng + I] = R4;
-  } else {
-    const double bdt = a.b * a.dt;
+  if constexpr (MODE == 1) {
+    // q^{k+1} = a q^n + b q^k + b dt R with, in the box, the inverse mass
+    // folded into one coefficient: b dt R_v = c s_v (+ b dt S_v), c = b dt / M
+    const double c = SHELL ? a.bdt : a.bdt * minv;
     double y[5];
-    const double R[5] = {R0, R1, R2, R3, R4};
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double qk = (v == 0) ? rp : a.qk[v * Ng + I];
-      double t = fma(a.b, qk, bdt * R[v]);
-      if (a.a != 0.0) t = fma(a.a, a.qn[v * Ng + I], t);
-      y[v] = t;
-      a.out[v * Ng + I] = t;
-      bad |= nonfinite(t);
+      // first stage (a = 0, b = 1): t = q^k; otherwise a q^n + b q^k
+      double t = a.first_stage ? qk : fma(a.a, a.qn[v * Ng + I], a.b * qk);
+      const double sv = v == 0 ? s0 : v == 1 ? s1 : v == 2 ? s2 : v == 3 ? s3 : s4;
+      if constexpr (!SHELL) {
+        // a wall removes the whole normal momentum tendency, source included
+        const bool walled = (v >= 1 && v <= 3) && (w & (1 << (v - 1)));
+        if (v == 3 && !walled) t = fma(-rp, a.bdtg, t);  // buoyancy -rho' g
+        y[v] = walled ? t : fma(c, sv, t);
+      } else {
+        y[v] = fma(c, sv, t);
+      }
+      a.out[v * Ng + I] = y[v];
+      bad |= nonfinite(y[v]);
     }
     if (bad) atomicOr(a.flag, 1);
     write_prim(a.pa, I, y[0], y[1], y[2], y[3], y[4]);

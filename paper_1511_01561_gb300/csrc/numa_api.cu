@@ -95,6 +95,9 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   a.a = ra;
   a.b = rb;
   a.dt = dt;
+  a.bdt = rb * dt;
+  a.bdtg = rb * dt * c->cfg.g;
+  a.first_stage = (ra == 0.0 && rb == 1.0) ? 1 : 0;
   a.mode = mode;
   a.flag = c->L.flags;
   a.pa = prim_args(c, nullptr, c->L.prim);

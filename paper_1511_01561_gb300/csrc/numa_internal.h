@@ -110,6 +110,8 @@ struct UpdateArgs {
   double g;            // box gravity
   double two_omega;    // shell Coriolis 2 Omega
   double a, b, dt;     // out = a qn + b (qk + dt R)
+  double bdt, bdtg;    // b dt and b dt g, computed once on the host
+  int first_stage;     // 1 when a = 0 and b = 1 (no q^n term)
   int mode;            // 0: write R, 1: RK stage (also writes the primitives of out)
   int* flag;           // non-finite flag
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
