@@ -43,6 +43,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--serve", action="store_true", help="ensemble-serving workload instead of the RK3 steps")
+    p.add_argument("--serve-requests", type=int, default=64)
+    p.add_argument("--serve-steps-scale", type=float, default=1.0, help="scale every request's step count")
+    p.add_argument("--serve-budget-frac", type=float, default=0.5, help="arena = this fraction of free HBM")
+    p.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate / saturated request rate")
     return p.parse_args()
 
 
@@ -333,12 +338,85 @@ def run_mine(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Ensemble serving: a seeded stream of rising-bubble forecast requests
+    (edge 8..48 elements, N in {3, 4, 6}, 100..1000 steps, FP64 or FP32-mixed)
+    served with continuous batching.  First all requests at once (saturated
+    request rate), then a Poisson stream at serve_load times that rate;
+    reports p50/p99 time-to-forecast and aggregate node-updates/s."""
+    import torch
+
+    from paper_1511_01561_gb300 import inputs as I
+    from paper_1511_01561_gb300 import numa
+
+    torch.cuda.set_device(0)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(args.serve_budget_frac * free) // 256 * 256
+    reqs = I.serving_stream(n=args.serve_requests)
+    for r in reqs:
+        r["nsteps"] = max(1, int(round(r["nsteps"] * args.serve_steps_scale)))
+
+    def node_count(cfg):
+        return (cfg["ne"][0] * cfg["N"] + 1) * (cfg["ne"][1] * cfg["N"] + 1) * (cfg["ne"][2] * cfg["N"] + 1)
+
+    work = sum(node_count(r["cfg"]) * STAGES * r["nsteps"] for r in reqs)
+
+    def serve(arrivals):
+        sched = numa.Scheduler(budget, build_threads=min(8, os.cpu_count() or 1))
+        t0 = time.perf_counter()
+        pending = sorted(range(len(reqs)), key=lambda i: arrivals[i])
+        ids, done_at, max_active = {}, {}, 0
+        while len(done_at) < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and arrivals[pending[0]] <= now:
+                i = pending.pop(0)
+                r = reqs[i]
+                ids[i] = sched.submit(r["cfg"], r["ic"], r["params"], r["dt"], r["nsteps"], r["precision"])
+            active, waiting = sched.step()
+            max_active = max(max_active, active)
+            now = time.perf_counter() - t0
+            for i, rid in ids.items():
+                if i not in done_at and sched.poll(rid)[0] in ("done", "failed"):
+                    done_at[i] = now
+            if active == 0 and waiting == 0 and pending:
+                time.sleep(max(0.0, min(0.05, arrivals[pending[0]] - now)))
+        makespan = max(done_at.values()) - min(arrivals)
+        ttf = sorted(done_at[i] - arrivals[i] for i in range(len(reqs)))
+        statuses = [sched.poll(ids[i])[0] for i in range(len(reqs))]
+        sched.close()
+        return dict(makespan_s=makespan, p50_s=float(np.percentile(ttf, 50)), p99_s=float(np.percentile(ttf, 99)),
+                    node_updates_per_s=work / makespan, max_active=max_active,
+                    failed=sum(st == "failed" for st in statuses))
+
+    import numpy as np
+
+    sat = serve([0.0] * len(reqs))
+    rate = args.serve_load * len(reqs) / sat["makespan_s"]
+    gaps = np.array([r["gap"] for r in reqs]) / rate
+    arr = list(np.cumsum(gaps) - gaps[0])
+    poi = serve(arr)
+    print(json.dumps({
+        "metric": "ensemble time-to-forecast p50/p99 and aggregate node-updates/s", "unit": "s",
+        "p50": poi["p50_s"], "p99": poi["p99_s"], "value": poi["node_updates_per_s"],
+        "value_unit": UNIT, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": "bubble ensemble stream", "requests": len(reqs), "seed": 1511,
+                   "edge": [8, 48], "N": [3, 4, 6], "steps_scale": args.serve_steps_scale,
+                   "arena_bytes": budget, "arena_frac_of_free": args.serve_budget_frac,
+                   "poisson_rate_per_s": rate, "load": args.serve_load,
+                   "fp32_mixed_requests": sum(r["precision"] == "fp32_mixed" for r in reqs),
+                   "total_node_updates": work},
+        "saturated": sat, "poisson": poi,
+    }))
+
+
 def main():
     args = parse()
     if args.cpu_worker:
         cpu_worker(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_mine(args)
 

@@ -164,6 +164,57 @@ int numa_time_kernels(numa_ctx* ctx, double dt, int nsteps, double* ms_volume, d
  * Waits for the stream. *flag = 0 or 1. */
 int numa_check_finite(numa_ctx* ctx, int* flag);
 
+/* ---- Serving: continuous batching of ensemble members ---------------------
+ * Not in the paper: many independent forecasts (members of different mesh
+ * sizes, orders, precisions and step counts) share one GPU.  Members advance
+ * together, one SSP-RK3 step per numa_sched_step, through ragged kernels that
+ * cover the elements and nodes of all admitted members; requests that arrive
+ * while others run are admitted as soon as their workspace fits. */
+typedef struct numa_sched numa_sched;
+
+enum numa_req_status {
+  NUMA_REQ_QUEUED = 0,   /* waiting for its mesh or for room in the arena */
+  NUMA_REQ_RUNNING = 1,  /* admitted, advancing */
+  NUMA_REQ_DONE = 2,     /* finished; fetch with numa_sched_result */
+  NUMA_REQ_FAILED = 3,   /* setup failed or the state became non-finite */
+  NUMA_REQ_CANCELLED = 4
+};
+
+/* Create a scheduler over a caller-owned device arena (256-byte aligned) used
+ * for all member workspaces and the scheduler's own tables, the compute
+ * stream (cudaStream_t as void*), and build_threads host threads that build
+ * meshes in the background.  The library still allocates no device memory. */
+int numa_sched_create(void* dev_arena, size_t arena_bytes, void* stream, int build_threads, numa_sched** out);
+
+/* Queue one forecast: mesh/physics/precision config, initial condition (as
+ * numa_init_state), time step and number of RK3 steps.  *id receives its
+ * handle.  NUMA_EBUDGET if its workspace can never fit in the arena. */
+int numa_sched_submit(numa_sched* s, const numa_config* cfg, int ic_kind, const double* params, int nparams,
+                      double dt, int nsteps, long long* id);
+
+/* Admit what fits (arrival order, first fit), advance every admitted member
+ * by one RK3 step (asynchronously, on the compute stream), retire members that
+ * reached their step count.  *n_active: members advancing; *n_waiting:
+ * requests queued, building or still copying their result out. */
+int numa_sched_step(numa_sched* s, int* n_active, int* n_waiting);
+
+/* Status (numa_req_status), steps done and global-node count of a request
+ * (steps_done and Ng may be NULL). */
+int numa_sched_poll(numa_sched* s, long long id, int* status, int* steps_done, long long* Ng);
+
+/* Copy a finished request's final state, double[5][Ng] host (n = 5*Ng), and
+ * forget the request.  NUMA_ENONFINITE (after copying) if it failed that way. */
+int numa_sched_result(numa_sched* s, long long id, double* q_host, long long n);
+
+/* Cancel a request that is still queued. */
+int numa_sched_cancel(numa_sched* s, long long id);
+
+const char* numa_sched_last_error(const numa_sched* s);
+
+/* Wait for the compute stream, free all host-side state.  Never frees the
+ * arena. */
+int numa_sched_destroy(numa_sched* s);
+
 /* Host copy of the global-node coordinates, double[3][Ng] (x, y, z). */
 int numa_get_coords(const numa_ctx* ctx, double* xyz);
 

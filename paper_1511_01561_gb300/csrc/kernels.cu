@@ -137,11 +137,13 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
 // Field slots of the 13 unique flux components staged per element node.
 enum : int { kUx = 0, kUy, kUz, kTxx, kTxy, kTxz, kTyy, kTyz, kTzz, kPp, kHx, kHy, kHz, kNF };
 
+// create_rhs of element e of one mesh, by the whole CTA (one thread per
+// element node); smem_raw holds kNF*(N+1)^3 + (N+1)^2 values of T.  Shared by
+// the single-mesh kernel and the ragged multi-member kernel, so that a member
+// computes bit for bit the same alone and in a mix.
 template <int N, typename T>
-__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
-    volume_kernel(VolumeArgs a) {
+__device__ __forceinline__ void volume_element(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   constexpr int P = N + 1, NP = P * P * P;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* F = reinterpret_cast<T*>(smem_raw);  // [kNF][NP]
   T* Ds = F + kNF * NP;                     // [P][P]
   const T* Dg;
@@ -153,7 +155,6 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     Dg = reinterpret_cast<const T*>(a.D32);
     met = reinterpret_cast<const T*>(a.met32);
   }
-  const int e = blockIdx.x;
   const int l = threadIdx.x;
   for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
   const long long n = (long long)e * NP + l;
@@ -254,16 +255,23 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
   re[4 * Nl + n] = -(jw * div_t);
 }
 
+template <int N, typename T>
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+    volume_kernel(VolumeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  volume_element<N, T>(a, blockIdx.x, smem_raw);
+}
+
 template <typename RT>
 __device__ __forceinline__ double re_load(const void* re, long long idx) {
   if constexpr (sizeof(RT) == 8) return static_cast<const double*>(re)[idx];
   else return f2d(static_cast<const float*>(re)[idx]);
 }
 
+// DSS, inverse mass, sources, walls and the stage update at global node I of
+// one mesh (shared by the single-mesh and the ragged kernels).
 template <int MODE, bool SHELL, typename RT>
-__global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
-  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= a.Ng) return;
+__device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
   const long long Ng = a.Ng, Nl = a.Nl;
   // direct stiffness summation in ascending element-node order (Eq. 4), FP64;
   // every global node has at least one element node
@@ -346,6 +354,60 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
   }
 }
 
+template <int MODE, bool SHELL, typename RT>
+__global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
+  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < a.Ng) update_node<MODE, SHELL, RT>(a, I);
+}
+
+// ---- ragged multi-member kernels (serving) ---------------------------------
+// Persistent kernels over the concatenated elements (or global nodes) of the
+// members of one group (same N, precision and mesh kind); the group table
+// maps a position in the concatenation to (member, local index).  Each
+// member's work is done by the same element / node functions as above.
+
+__device__ __forceinline__ int ragged_find(const long long* prefix, int n, long long w) {
+  int lo = 0, hi = n - 1;  // last m with prefix[m] <= w
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+    volume_ragged(const MemberDesc* __restrict__ d, const RaggedGroup* __restrict__ g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_m;
+  __shared__ long long s_e;
+  const int n = g->n;
+  const long long total = n > 0 ? g->elem_prefix[n] : 0;
+  for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int m = ragged_find(g->elem_prefix, n, w);
+      s_m = g->member[m];
+      s_e = w - g->elem_prefix[m];
+    }
+    __syncthreads();
+    volume_element<N, T>(d[s_m].va, s_e, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <bool SHELL, typename RT>
+__global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restrict__ d,
+                                                     const RaggedGroup* __restrict__ g, int stage) {
+  const int n = g->n;
+  const long long total = n > 0 ? g->node_prefix[n] : 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
+    const int m = ragged_find(g->node_prefix, n, w);
+    update_node<1, SHELL, RT>(d[g->member[m]].ua[stage], w - g->node_prefix[m]);
+  }
+}
+
 template <int N, typename T>
 cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
@@ -408,6 +470,73 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   } else {
     if (f32) launch_update_m<1, float>(a, nb, nt, s);
     else launch_update_m<1, double>(a, nb, nt, s);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 1;
+  }
+  return n;
+}
+
+// Persistent launch: as many CTAs as fit on the GPU at once.
+template <int N, typename T>
+cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
+  constexpr int P = N + 1, NP = P * P * P;
+  constexpr int NT = (NP + 31) / 32 * 32;
+  const size_t smem = sizeof(T) * (kNF * NP + P * P);
+  static int grid = 0;
+  if (!grid) {
+    cudaError_t e = cudaFuncSetAttribute(volume_ragged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, volume_ragged<N, T>, NT, smem);
+    if (e != cudaSuccess) return e;
+    grid = (per_sm > 0 ? per_sm : 1) * sm_count();
+  }
+  volume_ragged<N, T><<<grid, NT, smem, s>>>(d, g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_volume_ragged_p(int N, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_volume_ragged_t<1, T>(d, g, s);
+    case 2: return launch_volume_ragged_t<2, T>(d, g, s);
+    case 3: return launch_volume_ragged_t<3, T>(d, g, s);
+    case 4: return launch_volume_ragged_t<4, T>(d, g, s);
+    case 5: return launch_volume_ragged_t<5, T>(d, g, s);
+    case 6: return launch_volume_ragged_t<6, T>(d, g, s);
+    case 7: return launch_volume_ragged_t<7, T>(d, g, s);
+    case 8: return launch_volume_ragged_t<8, T>(d, g, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_volume_ragged(int N, int precision, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
+  if (precision == NUMA_FP32_MIXED) return launch_volume_ragged_p<float>(N, d, g, s);
+  return launch_volume_ragged_p<double>(N, d, g, s);
+}
+
+cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s) {
+  const int grid = 8 * sm_count();
+  const bool f32 = precision == NUMA_FP32_MIXED;
+  if (shell) {
+    if (f32) update_ragged<true, float><<<grid, 256, 0, s>>>(d, g, stage);
+    else update_ragged<true, double><<<grid, 256, 0, s>>>(d, g, stage);
+  } else {
+    if (f32) update_ragged<false, float><<<grid, 256, 0, s>>>(d, g, stage);
+    else update_ragged<false, double><<<grid, 256, 0, s>>>(d, g, stage);
   }
   return cudaGetLastError();
 }

@@ -12,22 +12,6 @@
 
 using namespace numa;
 
-struct numa_ctx {
-  numa_config cfg;
-  HostMesh mesh;
-  DevLayout L;
-  bool bound = false;
-  bool prim_valid = false;  // L.prim holds the primitive fields of L.q
-  cudaStream_t stream = nullptr;
-  std::string err;
-  double gamma = 1.4;
-  double eos[kEosTerms];
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  double graph_dt = NAN;
-  const double* graph_q = nullptr;
-};
-
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -43,7 +27,10 @@ int cuda_fail(numa_ctx* c, cudaError_t e, const char* what) {
   return fail(c, NUMA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// SSP-RK3 stage coefficients: q^{k+1} = a_k q^n + b_k (q^k + dt R(q^k))
+}  // namespace
+
+namespace numa {
+
 const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0};
 const double kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
 

@@ -121,4 +121,61 @@ cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s);
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s);
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 
+// ---- serving: ragged multi-member launches --------------------------------
+
+constexpr int kMaxMembers = 128;
+
+// Everything the element and node kernels need for one admitted member: its
+// volume arguments and its update arguments for each of the three stages.
+struct MemberDesc {
+  VolumeArgs va;
+  UpdateArgs ua[3];
+};
+
+// One group of members that share N, precision and mesh kind: prefix sums of
+// their element and global-node counts over the member slots in `member`.
+struct RaggedGroup {
+  int n;
+  int pad;
+  long long elem_prefix[kMaxMembers + 1];
+  long long node_prefix[kMaxMembers + 1];
+  int member[kMaxMembers];
+};
+
+cudaError_t launch_volume_ragged(int N, int precision, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s);
+cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s);
+
+}  // namespace numa
+
+// A context: the host mesh of one configuration and, once bound, the layout of
+// its device workspace.
+struct numa_ctx {
+  numa_config cfg;
+  numa::HostMesh mesh;
+  numa::DevLayout L;
+  bool bound = false;
+  bool prim_valid = false;  // L.prim holds the primitive fields of L.q
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double gamma = 1.4;
+  double eos[numa::kEosTerms];
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  const double* graph_q = nullptr;
+};
+
+namespace numa {
+
+// SSP-RK3 stage coefficients: q^{k+1} = a_k q^n + b_k (q^k + dt R(q^k))
+extern const double kRkA[3];
+extern const double kRkB[3];
+
+PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim);
+VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, void* re);
+UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, const double* qn, double* out,
+                       int mode, double ra, double rb, double dt);
+cudaError_t ensure_prim(numa_ctx* c);
+
 }  // namespace numa

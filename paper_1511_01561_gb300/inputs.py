@@ -62,6 +62,29 @@ WORKLOADS = {
 }
 
 
+def serving_stream(n: int = 64, seed: int = 1511, edge=(8, 48), orders=(3, 4, 6), amp=(0.1, 2.0),
+                   steps=(100, 1000), p_fp32: float = 0.5, L: float = 1000.0, r_c: float = 250.0) -> list:
+    """Forecast requests of the ensemble-serving workload: rising-bubble boxes
+    with edge ~ U{edge} elements per axis, order from `orders`, amplitude
+    ~ U(amp) K, centre uniform in the box at least r_c from every wall, step
+    count ~ U{steps}, FP32-mixed with probability p_fp32.  `gap` is the
+    request's exponential inter-arrival gap in units of the mean gap (a
+    Poisson stream once scaled by a rate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        ne = int(rng.integers(edge[0], edge[1] + 1))
+        N = int(rng.choice(orders))
+        A = float(rng.uniform(*amp))
+        c = rng.uniform(r_c, L - r_c, 3)
+        nsteps = int(rng.integers(steps[0], steps[1] + 1))
+        prec = "fp32_mixed" if rng.random() < p_fp32 else "fp64"
+        gap = float(rng.exponential(1.0))
+        out.append(dict(cfg=box(ne, N), ic="bubble", params=(A, r_c, float(c[0]), float(c[1]), float(c[2])),
+                        dt=0.01, nsteps=nsteps, precision=prec, gap=gap))
+    return out
+
+
 def random_perturbation(Ng: int, seed: int, rho=0.01, U=5.0, Theta=1.0) -> np.ndarray:
     """Uniform random nodal perturbations [5][Ng] of (rho', U_x, U_y, U_z, Theta')."""
     rng = np.random.default_rng(seed)

@@ -70,6 +70,14 @@ def _load():
         "numa_time_kernels": [vp, d, i, dp, dp],
         "numa_get_coords": [vp, dp],
         "numa_destroy": [vp],
+        "numa_sched_create": [vp, ctypes.c_size_t, vp, i, ctypes.POINTER(vp)],
+        "numa_sched_submit": [vp, ctypes.POINTER(numa_config), i, dp, i, d, i, ctypes.POINTER(ctypes.c_longlong)],
+        "numa_sched_step": [vp, ctypes.POINTER(i), ctypes.POINTER(i)],
+        "numa_sched_poll": [vp, ctypes.c_longlong, ctypes.POINTER(i), ctypes.POINTER(i),
+                            ctypes.POINTER(ctypes.c_longlong)],
+        "numa_sched_result": [vp, ctypes.c_longlong, dp, ctypes.c_longlong],
+        "numa_sched_cancel": [vp, ctypes.c_longlong],
+        "numa_sched_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -77,6 +85,8 @@ def _load():
         f.restype = ctypes.c_int
     L.numa_last_error.argtypes = [vp]
     L.numa_last_error.restype = ctypes.c_char_p
+    L.numa_sched_last_error.argtypes = [vp]
+    L.numa_sched_last_error.restype = ctypes.c_char_p
     return L
 
 
@@ -270,3 +280,101 @@ class Solver:
 
     def check_finite(self) -> int:
         return numa_check_finite(self.ctx)
+
+
+# ---- serving: continuous batching over one device arena --------------------
+
+REQ_STATUS = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+def _sched_check(s, rc: int):
+    if rc != NUMA_OK:
+        raise NumaError(rc, lib.numa_sched_last_error(s).decode() if s else "")
+
+
+def numa_sched_create(arena_ptr: int, arena_bytes: int, stream_ptr: int, build_threads: int = 4):
+    h = ctypes.c_void_p()
+    rc = lib.numa_sched_create(ctypes.c_void_p(arena_ptr), arena_bytes, ctypes.c_void_p(stream_ptr),
+                               build_threads, ctypes.byref(h))
+    if rc != NUMA_OK:
+        raise NumaError(rc, "numa_sched_create")
+    return h
+
+
+def numa_sched_submit(s, cfg: dict, ic: str, params=(), dt: float = 0.01, nsteps: int = 1,
+                      precision: str = "fp64") -> int:
+    c = make_config(cfg, precision)
+    p = (ctypes.c_double * max(1, len(params)))(*params)
+    rid = ctypes.c_longlong()
+    _sched_check(s, lib.numa_sched_submit(s, ctypes.byref(c), IC[ic], p, len(params), dt, nsteps, ctypes.byref(rid)))
+    return rid.value
+
+
+def numa_sched_step(s):
+    a, w = ctypes.c_int(), ctypes.c_int()
+    _sched_check(s, lib.numa_sched_step(s, ctypes.byref(a), ctypes.byref(w)))
+    return a.value, w.value
+
+
+def numa_sched_poll(s, rid: int):
+    """(status name, steps done, global-node count) of a request."""
+    st, done, ng = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _sched_check(s, lib.numa_sched_poll(s, rid, ctypes.byref(st), ctypes.byref(done), ctypes.byref(ng)))
+    return REQ_STATUS.get(st.value, st.value), done.value, ng.value
+
+
+def numa_sched_result(s, rid: int, Ng: int) -> np.ndarray:
+    q = np.zeros((5, Ng))
+    _sched_check(s, lib.numa_sched_result(s, rid, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5 * Ng))
+    return q
+
+
+def numa_sched_cancel(s, rid: int) -> None:
+    _sched_check(s, lib.numa_sched_cancel(s, rid))
+
+
+def numa_sched_destroy(s) -> None:
+    _sched_check(None, lib.numa_sched_destroy(s))
+
+
+class Scheduler:
+    """Continuous-batching ensemble server on one GPU: a torch-owned device
+    arena of `arena_bytes` holds every admitted member's workspace."""
+
+    def __init__(self, arena_bytes: int, device: str = "cuda:0", build_threads: int = 4, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=self.device)
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = numa_sched_create(base, int(arena_bytes), self.stream.cuda_stream, build_threads)
+
+    def submit(self, cfg: dict, ic: str, params=(), dt: float = 0.01, nsteps: int = 1, precision: str = "fp64"):
+        return numa_sched_submit(self.h, cfg, ic, params, dt, nsteps, precision)
+
+    def step(self):
+        """(active members, waiting requests) after one scheduler step."""
+        return numa_sched_step(self.h)
+
+    def poll(self, rid: int):
+        """(status, steps done, Ng)."""
+        return numa_sched_poll(self.h, rid)
+
+    def result(self, rid: int) -> np.ndarray:
+        return numa_sched_result(self.h, rid, self.poll(rid)[2])
+
+    def cancel(self, rid: int):
+        numa_sched_cancel(self.h, rid)
+
+    def close(self):
+        if getattr(self, "h", None):
+            numa_sched_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,117 @@
+"""GPU tests of the continuous-batching ensemble server (numa_sched_*):
+members of different sizes, orders, precisions and step counts, arriving
+while others run, give the same result in the mix as alone; admission waits
+for room in the arena; over-budget, poisoned and cancelled requests neither
+disturb the others nor trap the GPU."""
+import numpy as np
+import pytest
+
+from paper_1511_01561_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def numa():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_01561_gb300 import build
+    build.build()
+    from paper_1511_01561_gb300 import numa as mod
+    return mod
+
+
+REQUESTS = [
+    # cfg, initial condition, params, dt, steps, precision
+    (I.box(3, 4), "bubble", I.BUBBLE_PARAMS, 0.01, 7, "fp64"),
+    (I.box((2, 3, 2), 3), "bubble", (1.5, 200.0, 400.0, 600.0, 300.0), 0.01, 12, "fp32_mixed"),
+    (I.box(2, 6), "bubble", (2.0, 300.0, 500.0, 500.0, 400.0), 0.01, 5, "fp64"),
+    (I.box(4, 4), "bubble", (0.3, 250.0, 450.0, 520.0, 350.0), 0.01, 9, "fp64"),
+    (I.shell(2, 1, 3), "jetwave", I.JETWAVE_PARAMS, 1.0, 4, "fp64"),
+    (I.box((3, 2, 2), 4), "bubble", (0.8, 250.0, 500.0, 300.0, 300.0), 0.01, 0, "fp32_mixed"),
+]
+
+
+def _alone(numa, cfg, ic, params, dt, steps, precision):
+    s = numa.Solver(cfg, precision)
+    try:
+        s.init_state(ic, params)
+        s.run(dt, steps)
+        return s.get_state().numpy().copy()
+    finally:
+        s.close()
+
+
+def _drain(sched, ids, max_steps=2000):
+    for _ in range(max_steps):
+        sched.step()
+        if all(sched.poll(i)[0] in ("done", "failed", "cancelled") for i in ids):
+            return
+    raise AssertionError("scheduler did not finish")
+
+
+def _close(a, b):
+    scale = np.maximum(np.abs(b).max(axis=1, keepdims=True), 1e-300)
+    return np.all(np.abs(a - b) <= 1e-12 * scale)
+
+
+def test_mix_equals_alone_with_arrivals(numa):
+    sched = numa.Scheduler(512 << 20, build_threads=3)
+    try:
+        ids = [sched.submit(*r[:2], params=r[2], dt=r[3], nsteps=r[4], precision=r[5]) for r in REQUESTS[:3]]
+        for _ in range(3):  # later arrivals join a running batch
+            sched.step()
+        ids += [sched.submit(*r[:2], params=r[2], dt=r[3], nsteps=r[4], precision=r[5]) for r in REQUESTS[3:]]
+        _drain(sched, ids)
+        for rid, r in zip(ids, REQUESTS):
+            status, done, _ = sched.poll(rid)
+            assert status == "done" and done == r[4], (r, status, done)
+            got = sched.result(rid)
+            ref = _alone(numa, *r)
+            assert _close(got, ref), r
+    finally:
+        sched.close()
+
+
+def test_admission_waits_for_room(numa):
+    cfg = I.box(3, 4)
+    ctx = numa.numa_create(cfg)
+    need = numa.numa_get_mesh_info(ctx)["workspace_bytes"]
+    numa.numa_destroy(ctx)
+    sched = numa.Scheduler(int(1.5 * need) + (4 << 20), build_threads=2)  # room for one member at a time
+    try:
+        ids = [sched.submit(cfg, "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=n) for n in (3, 4, 2)]
+        max_active = 0
+        for _ in range(100):
+            active, _ = sched.step()
+            max_active = max(max_active, active)
+            if all(sched.poll(i)[0] == "done" for i in ids):
+                break
+        assert max_active == 1
+        for rid, n in zip(ids, (3, 4, 2)):
+            assert _close(sched.result(rid), _alone(numa, cfg, "bubble", I.BUBBLE_PARAMS, 0.01, n, "fp64"))
+        with pytest.raises(numa.NumaError) as e:
+            sched.submit(I.box(6, 4), "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=1)
+        assert e.value.code == -6  # NUMA_EBUDGET
+    finally:
+        sched.close()
+
+
+def test_poisoned_and_cancelled_requests_do_not_disturb_others(numa):
+    sched = numa.Scheduler(256 << 20, build_threads=2)
+    try:
+        good = sched.submit(I.box(3, 3), "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=6)
+        bad = sched.submit(I.box(2, 3), "bubble", (float("nan"), 250.0, 500.0, 500.0, 350.0), dt=0.01, nsteps=4)
+        gone = sched.submit(I.box(5, 4), "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=50)
+        sched.cancel(gone)
+        _drain(sched, [good, bad, gone])
+        assert sched.poll(gone)[0] == "cancelled"
+        assert sched.poll(bad)[0] == "failed"
+        with pytest.raises(numa.NumaError) as e:
+            sched.result(bad)
+        assert e.value.code == -4  # NUMA_ENONFINITE
+        assert sched.poll(good)[0] == "done"
+        assert _close(sched.result(good), _alone(numa, I.box(3, 3), "bubble", I.BUBBLE_PARAMS, 0.01, 6, "fp64"))
+    finally:
+        sched.close()
