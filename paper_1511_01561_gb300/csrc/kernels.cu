@@ -391,7 +391,9 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
       s_e = w - g->elem_prefix[m];
     }
     __syncthreads();
-    volume_element<N, T>(d[s_m].va, s_e, smem_raw);
+    // (uniform across the CTA) guard against a table that disagrees with the member
+    if (s_m >= 0 && s_m < kMaxMembers && s_e >= 0 && s_e < d[s_m].va.Ne)
+      volume_element<N, T>(d[s_m].va, s_e, smem_raw);
     __syncthreads();
   }
 }
@@ -404,7 +406,10 @@ __global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restric
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
     const int m = ragged_find(g->node_prefix, n, w);
-    update_node<1, SHELL, RT>(d[g->member[m]].ua[stage], w - g->node_prefix[m]);
+    const int slot = g->member[m];
+    const long long I = w - g->node_prefix[m];
+    if (slot >= 0 && slot < kMaxMembers && I >= 0 && I < d[slot].ua[stage].Ng)
+      update_node<1, SHELL, RT>(d[slot].ua[stage], I);
   }
 }
 

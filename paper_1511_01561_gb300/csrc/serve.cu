@@ -142,6 +142,7 @@ struct numa_sched {
   RaggedGroup* h_groups = nullptr;
   cudaEvent_t tables_copied = nullptr;
   bool tables_dirty = true;
+  bool need_rebuild = false;  // members retired: rebuild the tables before the next launch
   std::deque<cudaEvent_t> inflight;  // one event per launched step, at most kMaxInflight
   std::vector<cudaEvent_t> spare_events;
   std::vector<GroupKey> groups;  // group index -> key
@@ -411,7 +412,10 @@ int numa_sched_step(numa_sched* s, int* n_active, int* n_waiting) {
   }
   // 3. advance every active member by one RK step
   if (!s->active.empty()) {
-    if (changed) rebuild_tables(s);
+    if (changed || s->need_rebuild) {
+      rebuild_tables(s);
+      s->need_rebuild = false;
+    }
     e = upload_tables(s);
     if (e == cudaSuccess && (!s->graph || s->graph_groups != s->groups)) {
       if (s->graph) {
@@ -470,7 +474,9 @@ int numa_sched_step(numa_sched* s, int* n_active, int* n_waiting) {
     if (a != s->active.end()) s->active.erase(a);
     s->retiring.push_back(id);
   }
-  if (!finished.empty()) rebuild_tables(s);
+  // The pinned table mirrors may still be in flight to the device for the
+  // step just launched: rebuild them at the next step, after the upload event.
+  if (!finished.empty()) s->need_rebuild = true;
   if (n_active) *n_active = (int)s->active.size();
   if (n_waiting) *n_waiting = (int)(s->built.size() + s->to_build.size() + s->retiring.size());
   return NUMA_OK;

@@ -69,7 +69,9 @@ def serving_stream(n: int = 64, seed: int = 1511, edge=(8, 48), orders=(3, 4, 6)
     ~ U(amp) K, centre uniform in the box at least r_c from every wall, step
     count ~ U{steps}, FP32-mixed with probability p_fp32.  `gap` is the
     request's exponential inter-arrival gap in units of the mean gap (a
-    Poisson stream once scaled by a rate)."""
+    Poisson stream once scaled by a rate).  The time step keeps an acoustic
+    Courant number of 0.5 on the closest node pair, taken as
+    (L/edge)(1 - cos(pi/N))/2 at 350 m/s (at most 0.01 s)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n):
@@ -80,8 +82,10 @@ def serving_stream(n: int = 64, seed: int = 1511, edge=(8, 48), orders=(3, 4, 6)
         nsteps = int(rng.integers(steps[0], steps[1] + 1))
         prec = "fp32_mixed" if rng.random() < p_fp32 else "fp64"
         gap = float(rng.exponential(1.0))
+        dx_min = (L / ne) * 0.5 * (1.0 - math.cos(math.pi / N))
+        dt = min(0.01, 0.5 * dx_min / 350.0)
         out.append(dict(cfg=box(ne, N), ic="bubble", params=(A, r_c, float(c[0]), float(c[1]), float(c[2])),
-                        dt=0.01, nsteps=nsteps, precision=prec, gap=gap))
+                        dt=dt, nsteps=nsteps, precision=prec, gap=gap))
     return out
 
 

@@ -75,11 +75,12 @@ def test_mix_equals_alone_with_arrivals(numa):
 
 
 def test_admission_waits_for_room(numa):
-    cfg = I.box(3, 4)
+    cfg = I.box(6, 4)
     ctx = numa.numa_create(cfg)
     need = numa.numa_get_mesh_info(ctx)["workspace_bytes"]
     numa.numa_destroy(ctx)
-    sched = numa.Scheduler(int(1.5 * need) + (4 << 20), build_threads=2)  # room for one member at a time
+    # room for one member at a time (the scheduler's own tables take < 1 MiB)
+    sched = numa.Scheduler(int(1.5 * need) + (1 << 20), build_threads=2)
     try:
         ids = [sched.submit(cfg, "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=n) for n in (3, 4, 2)]
         max_active = 0
@@ -92,7 +93,7 @@ def test_admission_waits_for_room(numa):
         for rid, n in zip(ids, (3, 4, 2)):
             assert _close(sched.result(rid), _alone(numa, cfg, "bubble", I.BUBBLE_PARAMS, 0.01, n, "fp64"))
         with pytest.raises(numa.NumaError) as e:
-            sched.submit(I.box(6, 4), "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=1)
+            sched.submit(I.box(9, 4), "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=1)
         assert e.value.code == -6  # NUMA_EBUDGET
     finally:
         sched.close()
