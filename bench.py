@@ -330,6 +330,18 @@ def run_mine(args):
             "update_ms_avg": upd32 / nlaunch,
             "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
         }
+    if not args.no_fp32:
+        # FP64-accurate element kernel on the FP32 units ((hi, lo) float pairs)
+        msp, volp, updp, _, _, _, finp = measure("fp64_pairs")
+        vp = world * Ng * STAGES * args.steps / (msp * 1e-3)
+        volp_s = volp * 1e-3 / nlaunch
+        bp = volume_bytes(Nl, Ng, 8)
+        line["fp64_pairs"] = {
+            "value": vp, "unit": UNIT, "ms_per_step": msp / args.steps, "speedup_vs_fp64": vp / value,
+            "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
+            "volume_fp64_equiv_tflops": flops / volp_s / 1e12,
+            "volume_hbm_gbs": bp / volp_s / 1e9, "volume_hbm_frac": bp / volp_s / 1e9 / hbm_gbs,
+        }
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

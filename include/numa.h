@@ -54,9 +54,14 @@ enum numa_mesh_kind { NUMA_MESH_BOX = 0, NUMA_MESH_SHELL = 1 };
 enum numa_ref_kind { NUMA_REF_ISENTROPIC = 0, NUMA_REF_ISOTHERMAL = 1 };
 enum numa_precision {
   NUMA_FP64 = 0,      /* every step in FP64 */
-  NUMA_FP32_MIXED = 1 /* fluxes, metric terms and D contractions in FP32;
-                         state, EOS reference subtraction, DSS, inverse mass
-                         and the RK combination in FP64 */
+  NUMA_FP32_MIXED = 1, /* fluxes, metric terms and D contractions in FP32;
+                          state, EOS reference subtraction, DSS, inverse mass
+                          and the RK combination in FP64 */
+  NUMA_FP64_PAIRS = 2  /* FP64-accurate element kernel computed on the FP32
+                          units: every value is an unevaluated sum of two
+                          floats (about 48 significant bits), products by
+                          error-free FMA splits, sums by TwoSum; state,
+                          primitives/EOS, DSS, inverse mass and RK in FP64 */
 };
 enum numa_ic_kind { NUMA_IC_REST = 0, NUMA_IC_BUBBLE = 1, NUMA_IC_UNIFORM = 2, NUMA_IC_JETWAVE = 3 };
 

@@ -14,6 +14,7 @@
 // need FP64 stays off the FP64 pipe: float<->double conversions and the
 // finiteness test are done with integer operations on the bit patterns.
 #include <cstdint>
+#include <type_traits>
 
 #include "numa_internal.h"
 
@@ -21,6 +22,12 @@ namespace numa {
 namespace {
 
 // ---- FP64-pipe-free conversions -------------------------------------------
+// The rare cases (subnormal, infinite, NaN) go through out-of-line functions:
+// an inline fallback would be predicated into every call and issue its FP64
+// conversion on every lane whether taken or not.
+
+__device__ __noinline__ double f2d_rare(float f) { return (double)f; }
+__device__ __noinline__ float d2f_rare(double d) { return __double2float_rn(d); }
 
 // Exact float -> double.  Subnormal, infinite and NaN inputs take the
 // hardware conversion (zeros, common in a state at rest, do not).
@@ -28,7 +35,7 @@ __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ex = (u >> 23) & 0xffu;
   if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0u || ex == 0xffu) return (double)f;
+  if (ex == 0u || ex == 0xffu) return f2d_rare(f);
   const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
@@ -39,7 +46,7 @@ __device__ __forceinline__ float d2f(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);
   const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (ex <= 0 || ex >= 255) return __double2float_rn(d);
+  if (ex <= 0 || ex >= 255) return d2f_rare(d);
   // 52-bit fraction = (hi & 0xfffff) : lo; keep the top 23 bits, round on the other 29
   const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1fffffffu;
@@ -63,35 +70,106 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// ---- FP64 accuracy on the FP32 units ("pairs") ------------------------------
+// A value is the unevaluated sum h + l of two floats with |l| <= ulp(h)/2:
+// about 48 significant bits.  Products are formed with the FMA-based exact
+// product split (Dekker's two-product via FMA), sums with Knuth's TwoSum.
+
+struct Pairs {
+  float h, l;
+};
+
+// double -> pair with integer operations: h = the double's top 24 significant
+// bits (truncated), l = the next bits rounded to a float.  Zeros and values
+// outside float range (below 2^-74 the low part vanishes) take the FP64 path.
+__device__ __noinline__ Pairs split64_rare(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ Pairs split64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu);  // biased FP64 exponent
+  if (E < 1023 - 74 || E > 1023 + 127) return split64_rare(x);
+  const unsigned sign = hi & 0x80000000u;
+  const float h = __uint_as_float(sign | ((unsigned)(E - 1023 + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  // remainder: the low 29 fraction bits, weight 2^(E-1023-52)
+  const unsigned rem = lo & 0x1fffffffu;
+  const float r = __uint2float_rn(rem);  // rounds 29 -> 24 bits
+  const float scale = __uint_as_float((unsigned)(E - 1023 - 52 + 127) << 23);
+  const float l = r * scale;
+  return {h, sign ? -l : l};
+}
+
+// (h, l) pair -> double (exact: the pair fits in 53 bits).
+__device__ __forceinline__ double join64(Pairs a) { return f2d(a.h) + f2d(a.l); }
+
+__device__ __forceinline__ Pairs pp_mul(Pairs a, Pairs b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = p + e;
+  return {s, e - (s - p)};
+}
+
+// Unnormalised accumulator (sh, sl) += a * b.
+__device__ __forceinline__ void pp_fma(float& sh, float& sl, Pairs a, Pairs b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float t = (sh - (s - bb)) + (p - bb);
+  sl += t + e;
+  sh = s;
+}
+
+// First term of an accumulation: (sh, sl) = a * b.
+__device__ __forceinline__ void pp_first(float& sh, float& sl, Pairs a, Pairs b) {
+  sh = a.h * b.h;
+  float e = fmaf(a.h, b.h, -sh);
+  e = fmaf(a.h, b.l, e);
+  sl = fmaf(a.l, b.h, e);
+}
+
+__device__ __forceinline__ Pairs pp_norm(float sh, float sl) {
+  const float s = sh + sl;
+  return {s, sl - (s - sh)};
+}
+
+// a - b (TwoSum of the high parts, low parts added in).
+__device__ __forceinline__ Pairs pp_sub(Pairs a, Pairs b) {
+  const float s = a.h - b.h;
+  const float bb = s - a.h;
+  const float t = (a.h - (s - bb)) - (b.h + bb) + (a.l - b.l);
+  return pp_norm(s, t);
+}
+
+__device__ __noinline__ double eos_ratio_rare(double x, double gamma) { return expm1(gamma * log1p(x)); }
+__device__ __noinline__ float eos_ratio_f_rare(float x, float gamma) { return expm1f(gamma * log1pf(x)); }
+
 // (1+x)^gamma - 1 with full relative accuracy: the binomial series
 // sum_k C(gamma,k) x^k (Horner), 6 terms for |x| <= 2^-10 and 12 terms for
 // |x| <= 2^-5 (truncation below 1e-17 relative in both), else
-// expm1(gamma log1p(x)).
+// expm1(gamma log1p(x)).  The term count is a loop bound, not a branch, so
+// that the two series are never both issued.
 __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
-  const double ax = fabs(x);
-  if (ax <= 0.0009765625) {
-    double t = a.eos[5];
-#pragma unroll
-    for (int k = 4; k >= 0; --k) t = fma(t, x, a.eos[k]);
-    return t * x;
-  }
-  if (ax <= 0.03125) {
-    double t = a.eos[kEosTerms - 1];
-#pragma unroll
-    for (int k = kEosTerms - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
-    return t * x;
-  }
-  return expm1(a.gamma * log1p(x));
+  const unsigned hx = ((unsigned)__double2hiint(x)) & 0x7fffffffu;  // |x| by its high word
+  if (hx > 0x3fa00000u) return eos_ratio_rare(x, a.gamma);          // |x| > 2^-5
+  const int K = hx <= 0x3f500000u ? 6 : kEosTerms;                   // |x| <= 2^-10 : 6 terms
+  double t = a.eos[K - 1];
+  for (int k = K - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
+  return t * x;
 }
 
 __device__ __forceinline__ float eos_ratio_f(float x, const PrimArgs& a) {
-  if (fabsf(x) <= 0.03125f) {
-    float t = (float)a.eos[6];
+  if (fabsf(x) > 0.03125f) return eos_ratio_f_rare(x, (float)a.gamma);
+  float t = (float)a.eos[6];
 #pragma unroll
-    for (int k = 5; k >= 0; --k) t = fmaf(t, x, (float)a.eos[k]);
-    return t * x;
-  }
-  return expm1f((float)a.gamma * log1pf(x));
+  for (int k = 5; k >= 0; --k) t = fmaf(t, x, (float)a.eos[k]);
+  return t * x;
 }
 
 // Primitive fields of state (rp, U, Tp) at global node I (reference from a.ref):
@@ -116,6 +194,18 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     w[5 * Ng + I] = Uzf * rf;
     w[6 * Ng + I] = d2f(Th) * rf;
     w[7 * Ng + I] = d2f(p0) * eos_ratio_f(d2f(Tp) * d2f(iTh0), a);
+  } else if (a.precision == NUMA_FP64_PAIRS) {
+    // FP64 primitives, stored as (hi, lo) pairs for the element kernel
+    Pairs* w = static_cast<Pairs*>(a.prim);
+    const double r = rcp64(rho);
+    w[I] = split64(Ux);
+    w[Ng + I] = split64(Uy);
+    w[2 * Ng + I] = split64(Uz);
+    w[3 * Ng + I] = split64(Ux * r);
+    w[4 * Ng + I] = split64(Uy * r);
+    w[5 * Ng + I] = split64(Uz * r);
+    w[6 * Ng + I] = split64(Th * r);
+    w[7 * Ng + I] = split64(p0 * eos_ratio(Tp * iTh0, a));
   } else {
     double* w = static_cast<double*>(a.prim);
     const double r = rcp64(rho);
@@ -255,11 +345,123 @@ __device__ __forceinline__ void volume_element(const VolumeArgs& a, long long e,
   re[4 * Nl + n] = -(jw * div_t);
 }
 
+// create_rhs of element e in the pairs mode: the same steps as
+// volume_element, every value and product carried as a (hi, lo) float pair.
+template <int N>
+__device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  Pairs* F = reinterpret_cast<Pairs*>(smem_raw);  // [kNF][NP]
+  Pairs* Ds = F + kNF * NP;                         // [P][P]
+  Pairs* base = Ds + P * P;                         // [kNF]: the fluxes at element node 0
+  const Pairs* Dg = reinterpret_cast<const Pairs*>(a.D2);
+  const Pairs* met = reinterpret_cast<const Pairs*>(a.met2);
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
+  const long long n = e * NP + l;
+  const long long Ng = a.Ng, Nl = a.Nl;
+  Pairs v[kNF];
+  if (l < NP) {
+    const int g = a.l2g[n];
+    const Pairs* w = static_cast<const Pairs*>(a.prim);
+    const Pairs Ux = w[g], Uy = w[Ng + g], Uz = w[2 * Ng + g];
+    const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
+    const Pairs th = w[6 * Ng + g], pp = w[7 * Ng + g];
+    v[kUx] = Ux;
+    v[kUy] = Uy;
+    v[kUz] = Uz;
+    v[kTxx] = pp_mul(Ux, ux);
+    v[kTxy] = pp_mul(Ux, uy);
+    v[kTxz] = pp_mul(Ux, uz);
+    v[kTyy] = pp_mul(Uy, uy);
+    v[kTyz] = pp_mul(Uy, uz);
+    v[kTzz] = pp_mul(Uz, uz);
+    v[kPp] = pp;
+    v[kHx] = pp_mul(th, Ux);
+    v[kHy] = pp_mul(th, Uy);
+    v[kHz] = pp_mul(th, Uz);
+    if (l == 0) {
+#pragma unroll
+      for (int f = 0; f < kNF; ++f) base[f] = v[f];
+    }
+  }
+  __syncthreads();
+  // D annihilates constants, so the derivatives of F and of F - F(node 0)
+  // are the same; the differences keep their full relative accuracy in the
+  // contractions (no cancellation against the fields' common level).
+  if (l < NP) {
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) F[f * NP + l] = pp_sub(v[f], base[f]);
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  Pairs B[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + n];
+  const Pairs jw = met[9 * Nl + n];
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  // reference-space derivatives (Eq. 5) as normalised pairs
+  auto dref = [&](int f, Pairs& s0, Pairs& s1, Pairs& s2) {
+    const Pairs* Ff = F + f * NP;
+    float h0, l0, h1, l1, h2, l2;
+    pp_first(h0, l0, Ds[i * P], Ff[bx]);
+    pp_first(h1, l1, Ds[j * P], Ff[by]);
+    pp_first(h2, l2, Ds[k * P], Ff[bz]);
+#pragma unroll
+    for (int m = 1; m < P; ++m) {
+      pp_fma(h0, l0, Ds[i * P + m], Ff[bx + m]);
+      pp_fma(h1, l1, Ds[j * P + m], Ff[by + P * m]);
+      pp_fma(h2, l2, Ds[k * P + m], Ff[bz + P * P * m]);
+    }
+    s0 = pp_norm(h0, l0);
+    s1 = pp_norm(h1, l1);
+    s2 = pp_norm(h2, l2);
+  };
+  // chain rule: accumulate d/dx_c of a field into the unnormalised (dh, dl)
+  auto phys = [&](float& dh, float& dl, bool first, int c, Pairs s0, Pairs s1, Pairs s2) {
+    if (first) pp_first(dh, dl, s0, B[c]);
+    else pp_fma(dh, dl, s0, B[c]);
+    pp_fma(dh, dl, s1, B[3 + c]);
+    pp_fma(dh, dl, s2, B[6 + c]);
+  };
+  Pairs s0, s1, s2;
+  float rh, rl, xh, xl, yh, yl, zh, zl, th_, tl;
+  dref(kUx, s0, s1, s2); phys(rh, rl, true, 0, s0, s1, s2);
+  dref(kUy, s0, s1, s2); phys(rh, rl, false, 1, s0, s1, s2);
+  dref(kUz, s0, s1, s2); phys(rh, rl, false, 2, s0, s1, s2);
+  dref(kTxx, s0, s1, s2); phys(xh, xl, true, 0, s0, s1, s2);
+  dref(kTxy, s0, s1, s2); phys(xh, xl, false, 1, s0, s1, s2); phys(yh, yl, true, 0, s0, s1, s2);
+  dref(kTxz, s0, s1, s2); phys(xh, xl, false, 2, s0, s1, s2); phys(zh, zl, true, 0, s0, s1, s2);
+  dref(kTyy, s0, s1, s2); phys(yh, yl, false, 1, s0, s1, s2);
+  dref(kTyz, s0, s1, s2); phys(yh, yl, false, 2, s0, s1, s2); phys(zh, zl, false, 1, s0, s1, s2);
+  dref(kTzz, s0, s1, s2); phys(zh, zl, false, 2, s0, s1, s2);
+  dref(kPp, s0, s1, s2);
+  phys(xh, xl, false, 0, s0, s1, s2);
+  phys(yh, yl, false, 1, s0, s1, s2);
+  phys(zh, zl, false, 2, s0, s1, s2);
+  dref(kHx, s0, s1, s2); phys(th_, tl, true, 0, s0, s1, s2);
+  dref(kHy, s0, s1, s2); phys(th_, tl, false, 1, s0, s1, s2);
+  dref(kHz, s0, s1, s2); phys(th_, tl, false, 2, s0, s1, s2);
+  // element residual -Jw div F in FP64 (the pair is exact in a double)
+  double* re = static_cast<double*>(a.re);
+  re[n] = -join64(pp_mul(jw, pp_norm(rh, rl)));
+  re[Nl + n] = -join64(pp_mul(jw, pp_norm(xh, xl)));
+  re[2 * Nl + n] = -join64(pp_mul(jw, pp_norm(yh, yl)));
+  re[3 * Nl + n] = -join64(pp_mul(jw, pp_norm(zh, zl)));
+  re[4 * Nl + n] = -join64(pp_mul(jw, pp_norm(th_, tl)));
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  if constexpr (std::is_same<T, Pairs>::value) volume_element_pairs<N>(a, e, smem_raw);
+  else volume_element<N, T>(a, e, smem_raw);
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     volume_kernel(VolumeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  volume_element<N, T>(a, blockIdx.x, smem_raw);
+  element_rhs<N, T>(a, blockIdx.x, smem_raw);
 }
 
 template <typename RT>
@@ -393,7 +595,7 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     __syncthreads();
     // (uniform across the CTA) guard against a table that disagrees with the member
     if (s_m >= 0 && s_m < kMaxMembers && s_e >= 0 && s_e < d[s_m].va.Ne)
-      volume_element<N, T>(d[s_m].va, s_e, smem_raw);
+      element_rhs<N, T>(d[s_m].va, s_e, smem_raw);
     __syncthreads();
   }
 }
@@ -417,7 +619,7 @@ template <int N, typename T>
 cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = sizeof(T) * (kNF * NP + P * P);
+  const size_t smem = sizeof(T) * (kNF * NP + P * P + kNF);  // fluxes, D, base values (pairs)
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(volume_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -461,6 +663,7 @@ cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
 
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
   if (precision == NUMA_FP32_MIXED) return launch_volume_p<float>(N, a, s);
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_p<Pairs>(N, a, s);
   return launch_volume_p<double>(N, a, s);
 }
 
@@ -496,7 +699,7 @@ template <int N, typename T>
 cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = sizeof(T) * (kNF * NP + P * P);
+  const size_t smem = sizeof(T) * (kNF * NP + P * P + kNF);  // fluxes, D, base values (pairs)
   static int grid = 0;
   if (!grid) {
     cudaError_t e = cudaFuncSetAttribute(volume_ragged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -529,6 +732,7 @@ cudaError_t launch_volume_ragged_p(int N, const MemberDesc* d, const RaggedGroup
 
 cudaError_t launch_volume_ragged(int N, int precision, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
   if (precision == NUMA_FP32_MIXED) return launch_volume_ragged_p<float>(N, d, g, s);
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_p<Pairs>(N, d, g, s);
   return launch_volume_ragged_p<double>(N, d, g, s);
 }
 

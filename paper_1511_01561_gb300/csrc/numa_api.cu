@@ -55,6 +55,8 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.met32 = c->L.met32;
   a.D64 = c->L.D64;
   a.D32 = c->L.D32;
+  a.met2 = c->L.met2;
+  a.D2 = c->L.D2;
   a.re = re;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
@@ -151,9 +153,10 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.flags = (int*)take(64 * sizeof(int));
   d.q = (double*)take(5 * Ng * 8);
   d.qs = (double*)take(5 * Ng * 8);
-  d.prim = take(kPrimBytesPerNode * Ng);
+  d.prim = take(prim_bytes_per_node(c.precision) * Ng);
   d.re = take(residual_bytes(c, m));
   if (c.precision == NUMA_FP32_MIXED) d.met32 = (float*)take(10 * Nl * 4);
+  else if (c.precision == NUMA_FP64_PAIRS) d.met2 = (float2*)take(10 * Nl * 8);
   else d.met64 = (double*)take(10 * Nl * 8);
   d.l2g = (int32_t*)take(Nl * 4);
   d.csr_off = (int32_t*)take((Ng + 1) * 4);
@@ -167,6 +170,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   }
   d.D64 = (double*)take(PP * 8);
   d.D32 = (float*)take(PP * 4);
+  d.D2 = (float2*)take(PP * 8);
   d.bytes = off;
   if (L) *L = d;
   return off;
@@ -180,7 +184,7 @@ int rhs_with_scratch(numa_ctx* c, const double* q_dev, double* r_dev, double* sc
   if (!c || !q_dev || !r_dev || !scratch) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rhs_static_scratch before numa_bind");
   if ((const void*)q_dev == (const void*)r_dev) return fail(c, NUMA_EINVAL, "q and r must not alias");
-  const size_t prim_bytes = align_up(kPrimBytesPerNode * (size_t)c->mesh.Ng);
+  const size_t prim_bytes = align_up(prim_bytes_per_node(c->cfg.precision) * (size_t)c->mesh.Ng);
   const size_t need = prim_bytes + residual_bytes(c->cfg, c->mesh);
   if (need > 8 * (size_t)scratch_doubles)
     return fail(c, NUMA_EINVAL, "mesh needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
@@ -199,7 +203,8 @@ int numa_create(const numa_config* cfg, numa_ctx** out) {
   if (!out) return NUMA_EINVAL;
   *out = nullptr;
   if (!cfg) return NUMA_EINVAL;
-  if (cfg->precision != NUMA_FP64 && cfg->precision != NUMA_FP32_MIXED) return NUMA_EINVAL;
+  if (cfg->precision != NUMA_FP64 && cfg->precision != NUMA_FP32_MIXED && cfg->precision != NUMA_FP64_PAIRS)
+    return NUMA_EINVAL;
   if (!(cfg->cv > 0) || !(cfg->cp > cfg->cv) || !(cfg->Rd > 0) || !(cfg->P00 > 0)) return NUMA_EINVAL;
   numa_ctx* c = new (std::nothrow) numa_ctx();
   if (!c) return NUMA_ENOMEM;
@@ -249,18 +254,34 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   auto up = [&](void* dst, const void* src, size_t n) {
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
   };
-  std::vector<float> met32, D32;
+  std::vector<float> met32, D32, D2;
+  // (hi, lo) float pairs of FP64 values: hi = nearest float, lo = nearest
+  // float of the remainder
+  auto pairs_of = [](const std::vector<double>& v) {
+    std::vector<float> out(2 * v.size());
+    for (size_t t = 0; t < v.size(); ++t) {
+      const float h = (float)v[t];
+      out[2 * t] = h;
+      out[2 * t + 1] = (float)(v[t] - (double)h);
+    }
+    return out;
+  };
   if (c->cfg.precision == NUMA_FP32_MIXED) {
     met32.resize(m.met.size());
     for (size_t t = 0; t < m.met.size(); ++t) met32[t] = (float)m.met[t];
     up(L.met32, met32.data(), met32.size() * 4);
+  } else if (c->cfg.precision == NUMA_FP64_PAIRS) {
+    met32 = pairs_of(m.met);
+    up(L.met2, met32.data(), met32.size() * 4);
   } else {
     up(L.met64, m.met.data(), m.met.size() * 8);
   }
   D32.resize(m.D.size());
   for (size_t t = 0; t < m.D.size(); ++t) D32[t] = (float)m.D[t];
+  D2 = pairs_of(m.D);
   up(L.D64, m.D.data(), m.D.size() * 8);
   up(L.D32, D32.data(), D32.size() * 4);
+  up(L.D2, D2.data(), D2.size() * 4);
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
   up(L.csr_idx, m.csr_idx.data(), Nl * 4);

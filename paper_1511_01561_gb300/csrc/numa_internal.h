@@ -41,9 +41,12 @@ bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const do
 // Per-global-node primitive fields that the volume kernel gathers, written by
 // the stage update (or the primitive pass) for the state the next create_rhs
 // differentiates:
-//   FP64 mode : double [5][Ng] = u_x, u_y, u_z, theta, p'   (U comes from q)
-//   FP32 mode : float  [8][Ng] = U_x, U_y, U_z, u_x, u_y, u_z, theta, p'
-constexpr int kPrimBytesPerNode = 40;
+//   FP64 mode  : double [5][Ng] = u_x, u_y, u_z, theta, p'   (U comes from q)
+//   FP32 mode  : float  [8][Ng] = U_x, U_y, U_z, u_x, u_y, u_z, theta, p'
+//   pairs mode : float2 [8][Ng] = the same eight, each as a (hi, lo) pair
+inline int prim_bytes_per_node(int precision) {
+  return precision == NUMA_FP32_MIXED ? 32 : precision == NUMA_FP64_PAIRS ? 64 : 40;
+}
 
 // Device workspace carved from the caller's buffer.
 struct DevLayout {
@@ -53,6 +56,8 @@ struct DevLayout {
   void* re = nullptr;        // element residuals -Jw div F (scratch): double or float [5][Nl]
   double* met64 = nullptr;   // [10][Nl] FP64 metric terms and Jw
   float* met32 = nullptr;    // [10][Nl] FP32 copy (mixed-precision form)
+  float2* met2 = nullptr;    // [10][Nl] (hi, lo) pairs (pairs mode)
+  float2* D2 = nullptr;      // [P*P] (hi, lo) pairs (pairs mode)
   int32_t* l2g = nullptr;
   int32_t* csr_off = nullptr;
   int32_t* csr_idx = nullptr;
@@ -90,6 +95,8 @@ struct VolumeArgs {
   const float* met32;
   const double* D64;
   const float* D32;
+  const float2* met2;  // pairs mode
+  const float2* D2;    // pairs mode
   void* re;            // [5][Nl] output
   long long Ng, Nl;
   int Ne;

@@ -20,7 +20,7 @@ ERRORS = {-1: "NUMA_EINVAL", -2: "NUMA_ENOMEM", -3: "NUMA_ECUDA", -4: "NUMA_ENON
           -5: "NUMA_ETIMEOUT", -6: "NUMA_EBUDGET", -7: "NUMA_ESTATE"}
 MESH = {"box": 0, "shell": 1}
 REF = {"isentropic": 0, "isothermal": 1}
-PRECISION = {"fp64": 0, "fp32_mixed": 1}
+PRECISION = {"fp64": 0, "fp32_mixed": 1, "fp64_pairs": 2}
 IC = {"rest": 0, "bubble": 1, "uniform": 2, "jetwave": 3}
 
 

@@ -78,23 +78,28 @@ def _state(m, cfg, kind, seed):
     return q
 
 
+FP64_MODES = ["fp64", "fp64_pairs"]  # both held to the FP64 bars
+
+
+@pytest.mark.parametrize("precision", FP64_MODES)
 @pytest.mark.parametrize("name,cfg,kind", BOX_CASES, ids=[c[0] for c in BOX_CASES])
-def test_rhs_parity_box(numa, orc, name, cfg, kind):
+def test_rhs_parity_box(numa, orc, name, cfg, kind, precision):
     m = orc.Mesh(cfg)
     q = _state(m, cfg, kind, seed=zlib.crc32(name.encode()) % 1000)
     Ro = m.rhs(q)
-    Rg, xyz = _gpu_rhs(numa, cfg, q)
+    Rg, xyz = _gpu_rhs(numa, cfg, q, precision)
     assert np.abs(xyz - m.coords()).max() < 1e-9
     err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
     assert err.max() <= TOL_RHS, err
 
 
+@pytest.mark.parametrize("precision", FP64_MODES)
 @pytest.mark.parametrize("cfg", [I.shell(2, 2, 4), I.shell(3, 1, 3), I.shell(1, 2, 6, Omega=0.0)])
-def test_rhs_parity_shell(numa, orc, cfg):
+def test_rhs_parity_shell(numa, orc, cfg, precision):
     m = orc.Mesh(cfg)
     q = _state(m, cfg, "smooth", seed=5) + 0.1 * _state(m, cfg, "random", seed=6)
     Ro = m.rhs(q)
-    s = numa.Solver(cfg)
+    s = numa.Solver(cfg, precision)
     try:
         perm = match_nodes(s.coords(), m.coords(), tol=1e-3)
         Rg = s.rhs(np.ascontiguousarray(q[:, perm])).cpu().numpy()
@@ -133,14 +138,15 @@ def test_init_state_parity(numa, orc):
     assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
 
 
-def test_rk3_100_steps_bubble(numa, orc):
+@pytest.mark.parametrize("precision", FP64_MODES)
+def test_rk3_100_steps_bubble(numa, orc, precision):
     """Workload bubble_4x4x4_N4: 100 SSP-RK3 steps at dt = 0.01 s."""
     w = I.WORKLOADS["bubble_4x4x4_N4"]
     cfg = w["cfg"]
     m = orc.Mesh(cfg)
     q0 = m.init_state(*w["ic"])
     qo = m.run(q0, w["dt"], w["steps"])
-    s = numa.Solver(cfg)
+    s = numa.Solver(cfg, precision)
     try:
         s.set_state(q0)
         s.run(w["dt"], w["steps"])
@@ -158,7 +164,8 @@ def test_rk3_100_steps_bubble(numa, orc):
     assert np.abs(qo[3]).max() > 1e-4  # the bubble has started to rise
 
 
-def test_rk3_steps_shell_and_warped(numa, orc):
+@pytest.mark.parametrize("precision", FP64_MODES)
+def test_rk3_steps_shell_and_warped(numa, orc, precision):
     for cfg, dt, steps in ((I.shell(2, 2, 3), 2.0, 20), (I.box(2, 4, warp=0.05), 0.01, 30)):
         m = orc.Mesh(cfg)
         q0 = 0.3 * _state(m, cfg, "smooth", seed=9)
@@ -168,7 +175,7 @@ def test_rk3_steps_shell_and_warped(numa, orc):
             walls = (m.wall() & 8) != 0
             q0[1:4, walls] -= (q0[1:4, walls] * rhat[:, walls]).sum(0) * rhat[:, walls]
         qo = m.run(q0, dt, steps)
-        s = numa.Solver(cfg)
+        s = numa.Solver(cfg, precision)
         try:
             perm = match_nodes(s.coords(), m.coords(), tol=1e-3)
             s.set_state(np.ascontiguousarray(q0[:, perm]))
@@ -187,9 +194,11 @@ def test_full_size_bubble_rhs(numa, orc):
     m = orc.Mesh(cfg)
     q = m.init_state("bubble", I.BUBBLE_PARAMS) + 0.1 * _state(m, cfg, "smooth", seed=21)
     Ro = m.rhs(q)
-    Rg, _ = _gpu_rhs(numa, cfg, q)
-    err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
-    assert err.max() <= TOL_RHS, err
+    floors = rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max())
+    for precision in FP64_MODES:
+        Rg, _ = _gpu_rhs(numa, cfg, q, precision)
+        err = rel_errors(Rg, Ro, floors)
+        assert err.max() <= TOL_RHS, (precision, err)
 
 
 def test_nonfinite_flag_and_errors(numa):

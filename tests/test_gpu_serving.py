@@ -3,6 +3,8 @@ members of different sizes, orders, precisions and step counts, arriving
 while others run, give the same result in the mix as alone; admission waits
 for room in the arena; over-budget, poisoned and cancelled requests neither
 disturb the others nor trap the GPU."""
+import time
+
 import numpy as np
 import pytest
 
@@ -43,11 +45,18 @@ def _alone(numa, cfg, ic, params, dt, steps, precision):
         s.close()
 
 
-def _drain(sched, ids, max_steps=2000):
-    for _ in range(max_steps):
-        sched.step()
+def _drain(sched, ids, seconds=120.0):
+    """Step until every request has finished (meshes build in the background,
+    so idle steps wait a little instead of spinning)."""
+    deadline = time.time() + seconds
+    max_active = 0
+    while time.time() < deadline:
+        active, _ = sched.step()
+        max_active = max(max_active, active)
         if all(sched.poll(i)[0] in ("done", "failed", "cancelled") for i in ids):
-            return
+            return max_active
+        if active == 0:
+            time.sleep(0.005)
     raise AssertionError("scheduler did not finish")
 
 
@@ -60,8 +69,13 @@ def test_mix_equals_alone_with_arrivals(numa):
     sched = numa.Scheduler(512 << 20, build_threads=3)
     try:
         ids = [sched.submit(*r[:2], params=r[2], dt=r[3], nsteps=r[4], precision=r[5]) for r in REQUESTS[:3]]
-        for _ in range(3):  # later arrivals join a running batch
-            sched.step()
+        steps = 0
+        deadline = time.time() + 60
+        while steps < 3 and time.time() < deadline:  # later arrivals join a running batch
+            active, _ = sched.step()
+            steps += active > 0
+            if active == 0:
+                time.sleep(0.005)
         ids += [sched.submit(*r[:2], params=r[2], dt=r[3], nsteps=r[4], precision=r[5]) for r in REQUESTS[3:]]
         _drain(sched, ids)
         for rid, r in zip(ids, REQUESTS):
@@ -83,13 +97,7 @@ def test_admission_waits_for_room(numa):
     sched = numa.Scheduler(int(1.5 * need) + (1 << 20), build_threads=2)
     try:
         ids = [sched.submit(cfg, "bubble", I.BUBBLE_PARAMS, dt=0.01, nsteps=n) for n in (3, 4, 2)]
-        max_active = 0
-        for _ in range(100):
-            active, _ = sched.step()
-            max_active = max(max_active, active)
-            if all(sched.poll(i)[0] == "done" for i in ids):
-                break
-        assert max_active == 1
+        assert _drain(sched, ids) == 1
         for rid, n in zip(ids, (3, 4, 2)):
             assert _close(sched.result(rid), _alone(numa, cfg, "bubble", I.BUBBLE_PARAMS, 0.01, n, "fp64"))
         with pytest.raises(numa.NumaError) as e:
