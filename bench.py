@@ -68,9 +68,10 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # source they were taken on (first 16 hex digits of its sha256).
-NCU_TRAFFIC = {"kernels_sha256_16": "06adc693a78b32a9",
-               "volume_fp64": 481.590016e6 + 141.615616e6,
-               "volume_fp32": 317.665792e6 + 133.572352e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "360368949e549b56",
+               "volume_fp64": 481.620992e6 + 143.209472e6,
+               "volume_fp32": 248.970240e6 + 64.139008e6,
+               "volume_pairs": 481.579520e6 + 142.462208e6}
 
 
 def ncu_traffic(key: str):
@@ -339,7 +340,7 @@ def run_mine(args):
         line["fp64_pairs"] = {
             "value": vp, "unit": UNIT, "ms_per_step": msp / args.steps, "speedup_vs_fp64": vp / value,
             "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
-            "volume_fp64_equiv_tflops": flops / volp_s / 1e12,
+            "volume_fp64_equiv_tflops": flops / volp_s / 1e12, "volume_traffic": ncu_traffic("volume_pairs"),
             "volume_hbm_gbs": bp / volp_s / 1e9, "volume_hbm_frac": bp / volp_s / 1e9 / hbm_gbs,
         }
     if cpu is not None:
