@@ -359,13 +359,13 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
   const long long n = e * NP + l;
   const long long Ng = a.Ng, Nl = a.Nl;
-  Pairs v[kNF];
   if (l < NP) {
     const int g = a.l2g[n];
     const Pairs* w = static_cast<const Pairs*>(a.prim);
     const Pairs Ux = w[g], Uy = w[Ng + g], Uz = w[2 * Ng + g];
     const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
     const Pairs th = w[6 * Ng + g], pp = w[7 * Ng + g];
+    Pairs v[kNF];
     v[kUx] = Ux;
     v[kUy] = Uy;
     v[kUz] = Uz;
@@ -379,6 +379,8 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
     v[kHx] = pp_mul(th, Ux);
     v[kHy] = pp_mul(th, Uy);
     v[kHz] = pp_mul(th, Uz);
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) F[f * NP + l] = v[f];
     if (l == 0) {
 #pragma unroll
       for (int f = 0; f < kNF; ++f) base[f] = v[f];
@@ -387,10 +389,11 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   __syncthreads();
   // D annihilates constants, so the derivatives of F and of F - F(node 0)
   // are the same; the differences keep their full relative accuracy in the
-  // contractions (no cancellation against the fields' common level).
+  // contractions (no cancellation against the fields' common level).  Each
+  // thread rewrites only its own node's entries.
   if (l < NP) {
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) F[f * NP + l] = pp_sub(v[f], base[f]);
+    for (int f = 0; f < kNF; ++f) F[f * NP + l] = pp_sub(F[f * NP + l], base[f]);
   }
   __syncthreads();
   if (l >= NP) return;
@@ -451,6 +454,14 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   re[4 * Nl + n] = -join64(pp_mul(jw, pp_norm(th_, tl)));
 }
 
+// Dynamic shared memory of one element: the staged fluxes, D and (pairs
+// mode) the node-0 base values.
+template <int N, typename T>
+constexpr size_t element_smem_bytes() {
+  constexpr int P = N + 1, NP = P * P * P;
+  return sizeof(T) * (kNF * NP + P * P + kNF);
+}
+
 template <int N, typename T>
 __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   if constexpr (std::is_same<T, Pairs>::value) volume_element_pairs<N>(a, e, smem_raw);
@@ -471,7 +482,9 @@ __device__ __forceinline__ double re_load(const void* re, long long idx) {
 }
 
 // DSS, inverse mass, sources, walls and the stage update at global node I of
-// one mesh (shared by the single-mesh and the ragged kernels).
+// one mesh (shared by the single-mesh and the ragged kernels).  MODE 0 writes
+// the tendency R; MODE 1 a general RK stage; MODE 2 the first stage (a = 0,
+// b = 1: no q^n read, no q^n term).
 template <int MODE, bool SHELL, typename RT>
 __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
   const long long Ng = a.Ng, Nl = a.Nl;
@@ -528,7 +541,7 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
     s3 = R3;
     s4 = R4;
   }
-  if constexpr (MODE == 1) {
+  if constexpr (MODE >= 1) {
     // q^{k+1} = a q^n + b q^k + b dt R with, in the box, the inverse mass
     // folded into one coefficient: b dt R_v = c s_v (+ b dt S_v), c = b dt / M
     const double c = SHELL ? a.bdt : a.bdt * minv;
@@ -537,8 +550,10 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double qk = (v == 0) ? rp : a.qk[v * Ng + I];
-      // first stage (a = 0, b = 1): t = q^k; otherwise a q^n + b q^k
-      double t = a.first_stage ? qk : fma(a.a, a.qn[v * Ng + I], a.b * qk);
+      // first stage (MODE 2: a = 0, b = 1): t = q^k; otherwise a q^n + b q^k
+      double t;
+      if constexpr (MODE == 2) t = qk;
+      else t = fma(a.a, a.qn[v * Ng + I], a.b * qk);
       const double sv = v == 0 ? s0 : v == 1 ? s1 : v == 2 ? s2 : v == 3 ? s3 : s4;
       if constexpr (!SHELL) {
         // a wall removes the whole normal momentum tendency, source included
@@ -600,7 +615,7 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
   }
 }
 
-template <bool SHELL, typename RT>
+template <int MODE, bool SHELL, typename RT>
 __global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restrict__ d,
                                                      const RaggedGroup* __restrict__ g, int stage) {
   const int n = g->n;
@@ -611,7 +626,7 @@ __global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restric
     const int slot = g->member[m];
     const long long I = w - g->node_prefix[m];
     if (slot >= 0 && slot < kMaxMembers && I >= 0 && I < d[slot].ua[stage].Ng)
-      update_node<1, SHELL, RT>(d[slot].ua[stage], I);
+      update_node<MODE, SHELL, RT>(d[slot].ua[stage], I);
   }
 }
 
@@ -619,7 +634,7 @@ template <int N, typename T>
 cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = sizeof(T) * (kNF * NP + P * P + kNF);  // fluxes, D, base values (pairs)
+  const size_t smem = element_smem_bytes<N, T>();
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(volume_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -675,6 +690,9 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   if (a.mode == 0) {
     if (f32) launch_update_m<0, float>(a, nb, nt, s);
     else launch_update_m<0, double>(a, nb, nt, s);
+  } else if (a.first_stage) {
+    if (f32) launch_update_m<2, float>(a, nb, nt, s);
+    else launch_update_m<2, double>(a, nb, nt, s);
   } else {
     if (f32) launch_update_m<1, float>(a, nb, nt, s);
     else launch_update_m<1, double>(a, nb, nt, s);
@@ -699,7 +717,7 @@ template <int N, typename T>
 cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = sizeof(T) * (kNF * NP + P * P + kNF);  // fluxes, D, base values (pairs)
+  const size_t smem = element_smem_bytes<N, T>();
   static int grid = 0;
   if (!grid) {
     cudaError_t e = cudaFuncSetAttribute(volume_ragged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -740,13 +758,19 @@ cudaError_t launch_update_ragged(int precision, bool shell, int stage, const Mem
                                  cudaStream_t s) {
   const int grid = 8 * sm_count();
   const bool f32 = precision == NUMA_FP32_MIXED;
-  if (shell) {
-    if (f32) update_ragged<true, float><<<grid, 256, 0, s>>>(d, g, stage);
-    else update_ragged<true, double><<<grid, 256, 0, s>>>(d, g, stage);
-  } else {
-    if (f32) update_ragged<false, float><<<grid, 256, 0, s>>>(d, g, stage);
-    else update_ragged<false, double><<<grid, 256, 0, s>>>(d, g, stage);
-  }
+  auto go = [&](auto mode_tag) {
+    constexpr int M = decltype(mode_tag)::value;
+    if (shell) {
+      if (f32) update_ragged<M, true, float><<<grid, 256, 0, s>>>(d, g, stage);
+      else update_ragged<M, true, double><<<grid, 256, 0, s>>>(d, g, stage);
+    } else {
+      if (f32) update_ragged<M, false, float><<<grid, 256, 0, s>>>(d, g, stage);
+      else update_ragged<M, false, double><<<grid, 256, 0, s>>>(d, g, stage);
+    }
+  };
+  // stage 0 of SSP-RK3 is the first stage (a = 0, b = 1)
+  if (stage == 0) go(std::integral_constant<int, 2>());
+  else go(std::integral_constant<int, 1>());
   return cudaGetLastError();
 }
 
