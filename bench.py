@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--serve-steps-scale", type=float, default=1.0, help="scale every request's step count")
     p.add_argument("--serve-budget-frac", type=float, default=0.5, help="arena = this fraction of free HBM")
     p.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate / saturated request rate")
+    p.add_argument("--serve-overload", type=float, default=2.0,
+                   help="rate of a second Poisson stream / saturated request rate (0 skips it)")
     return p.parse_args()
 
 
@@ -81,17 +83,24 @@ def ncu_traffic(key: str):
     return NCU_TRAFFIC.get(key) if sha == NCU_TRAFFIC["kernels_sha256_16"] else None
 
 
-def volume_flops_per_elem_node(N: int) -> float:
-    """Algorithmic FP64 flops per element node of create_rhs: 39 contractions
-    of length N+1 (2 flops each) plus about 150 pointwise flops."""
-    return 78.0 * (N + 1) + 150.0
+def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
+    """Algorithmic flops per element node of create_rhs (an FMA counts 2).
+    Per-node form of Eq. 5: 39 contractions of length N+1 plus about 150
+    pointwise flops.  Affine-element form: 15 contractions of length N+1 plus
+    65 pointwise flops (per direction: B_d.u and B_d.U, 5 each; three momentum
+    fluxes U_x (B_d.u) + B_dx p', 3 each; theta (B_d.U), 1; then 5 products
+    with -Jw)."""
+    return 30.0 * (N + 1) + 65.0 if affine else 78.0 * (N + 1) + 150.0
 
 
-def volume_bytes(Nl: int, Ng: int, fp: int) -> float:
+def volume_bytes(Nl: int, Ng: int, fp: int, N: int = 4, affine: bool = False) -> float:
     """Algorithmic DRAM bytes of one volume-kernel launch (fp = 8 for FP64, 4
-    for the FP32-mixed form): metric terms and Jw (10 values per element node),
-    l2g (4 B), the residual write (5 values), and one read per global node of
-    the gathered fields (FP64: U and u, theta, p' = 8 doubles; FP32: 8 floats)."""
+    for the FP32-mixed form): metric terms and Jw (10 values per element
+    node; affine elements: Jw per node and 9 metric terms per element), l2g
+    (4 B), the residual write (5 values), and one read per global node of the
+    gathered fields (FP64: U and u, theta, p' = 8 doubles; FP32: 8 floats)."""
+    if affine:
+        return Nl * (fp + 4 + 5 * fp) + Nl // (N + 1) ** 3 * 9 * fp + Ng * 8 * fp
     return Nl * (10 * fp + 4 + 5 * fp) + Ng * 8 * fp
 
 
@@ -235,6 +244,9 @@ def run_mine(args):
     w = I.WORKLOADS[args.workload]
     cfg, dt = w["cfg"], w["dt"]
     hbm_gbs, peak_src = load_peaks()
+    # a box without warp has affine elements: the kernels take the
+    # contravariant-flux form unless the per-node form is asked for
+    affine = cfg["kind"] == "box" and float(cfg.get("warp", 0.0)) == 0.0
 
     def barrier():
         if dist is not None:
@@ -247,15 +259,15 @@ def run_mine(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def measure(precision):
-        s = numa.Solver(cfg, precision, device=str(dev))
+    def measure(precision, form="auto"):
+        s = numa.Solver(dict(cfg, metric_form=form), precision, device=str(dev))
         s.init_state(*w["ic"])
         s.run(dt, args.warmup)
         stream = s.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(local) if precision == "fp64" else None
+        clocks = ClockSampler(local) if (precision, form) == ("fp64", "auto") else None
         e0.record(stream)
         s.run(dt, args.steps)
         e1.record(stream)
@@ -267,7 +279,7 @@ def run_mine(args):
         ms_vol, ms_upd = s.time_kernels(dt, args.steps)
         info = s.info
         e2e = None
-        if not args.no_e2e and precision == "fp64":
+        if not args.no_e2e and (precision, form) == ("fp64", "auto"):
             q_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             out_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             s.get_state(q_host)
@@ -292,8 +304,9 @@ def run_mine(args):
     value = world * Ng * STAGES * args.steps / (ms * 1e-3)
     nlaunch = STAGES * args.steps
     vol_avg_s = ms_vol * 1e-3 / nlaunch
-    flops = volume_flops_per_elem_node(N) * Nl
+    flops = volume_flops_per_elem_node(N, affine) * Nl
     achieved_tf = flops / vol_avg_s / 1e12
+    form_name = "affine" if affine else "nodal"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -304,10 +317,11 @@ def run_mine(args):
                    "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
         "e2e": e2e,
         "gpu_launches": 2 * nlaunch,
-        "roofline": {"kernel": "volume_kernel<4,double>", "bound": "alu", "achieved": achieved_tf,
+        "roofline": {"kernel": f"volume_kernel<{N},double,{form_name}>", "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": ncu_traffic("volume_fp64"),
-                     "algorithmic_bytes": volume_bytes(Nl, Ng, 8),
+                     "traffic": ncu_traffic(f"volume_fp64_{form_name}"),
+                     "algorithmic_flops": flops,
+                     "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine),
                      "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
                      "avg_launch_ms": 1e3 * vol_avg_s,
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},
@@ -316,21 +330,44 @@ def run_mine(args):
         "clocks": ck,
         "finite": finite,
     }
+    if affine:
+        # the same workload through the per-node form of Eq. 5 (metric terms
+        # read and applied at every node), for comparison
+        msn, voln, updn, _, _, _, finn = measure("fp64", "nodal")
+        voln_s = voln * 1e-3 / nlaunch
+        fl_n = volume_flops_per_elem_node(N, False) * Nl
+        line["fp64_nodal_form"] = {
+            "value": world * Ng * STAGES * args.steps / (msn * 1e-3), "unit": UNIT, "ms_per_step": msn / args.steps,
+            "finite": finn, "volume_ms_avg": 1e3 * voln_s, "update_ms_avg": updn / nlaunch,
+            "roofline": {"kernel": f"volume_kernel<{N},double,nodal>", "bound": "alu",
+                         "achieved": fl_n / voln_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": fl_n / voln_s / 1e12 / FP64_PEAK_TFLOPS,
+                         "traffic": ncu_traffic("volume_fp64_nodal")},
+        }
     if not args.no_fp32:
         ms32, vol32, upd32, _, _, _, fin32 = measure("fp32_mixed")
         v32 = world * Ng * STAGES * args.steps / (ms32 * 1e-3)
         vol32_s = vol32 * 1e-3 / nlaunch
-        b = volume_bytes(Nl, Ng, 4)
+        b = volume_bytes(Nl, Ng, 4, N, affine)
         line["fp32_mixed"] = {
             "value": v32, "unit": UNIT, "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": v32 / value,
             "finite": fin32,
-            "roofline": {"kernel": "volume_kernel<4,float>", "bound": "hbm", "achieved": b / vol32_s / 1e9,
-                         "peak": hbm_gbs, "unit": "GB/s", "frac": b / vol32_s / 1e9 / hbm_gbs,
-                         "traffic": ncu_traffic("volume_fp32"), "algorithmic_bytes": b,
+            "roofline": {"kernel": f"volume_kernel<{N},float,{form_name}>", "bound": "hbm",
+                         "achieved": b / vol32_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": b / vol32_s / 1e9 / hbm_gbs,
+                         "traffic": ncu_traffic(f"volume_fp32_{form_name}"), "algorithmic_bytes": b,
                          "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
             "update_ms_avg": upd32 / nlaunch,
             "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
         }
+        if affine:
+            ms32n, vol32n, _, _, _, _, fin32n = measure("fp32_mixed", "nodal")
+            vol32n_s = vol32n * 1e-3 / nlaunch
+            bn = volume_bytes(Nl, Ng, 4)
+            line["fp32_mixed"]["nodal_form"] = {
+                "value": world * Ng * STAGES * args.steps / (ms32n * 1e-3), "ms_per_step": ms32n / args.steps,
+                "finite": fin32n, "volume_ms_avg": 1e3 * vol32n_s, "volume_hbm_frac": bn / vol32n_s / 1e9 / hbm_gbs,
+                "traffic": ncu_traffic("volume_fp32_nodal")}
     if not args.no_fp32:
         # FP64-accurate element kernel on the FP32 units ((hi, lo) float pairs)
         msp, volp, updp, _, _, _, finp = measure("fp64_pairs")
@@ -340,7 +377,8 @@ def run_mine(args):
         line["fp64_pairs"] = {
             "value": vp, "unit": UNIT, "ms_per_step": msp / args.steps, "speedup_vs_fp64": vp / value,
             "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
-            "volume_fp64_equiv_tflops": flops / volp_s / 1e12, "volume_traffic": ncu_traffic("volume_pairs"),
+            "volume_fp64_equiv_tflops": volume_flops_per_elem_node(N, False) * Nl / volp_s / 1e12,
+            "volume_traffic": ncu_traffic("volume_pairs"),
             "volume_hbm_gbs": bp / volp_s / 1e9, "volume_hbm_frac": bp / volp_s / 1e9 / hbm_gbs,
         }
     if cpu is not None:
@@ -355,7 +393,8 @@ def run_serve(args):
     """Ensemble serving: a seeded stream of rising-bubble forecast requests
     (edge 8..48 elements, N in {3, 4, 6}, 100..1000 steps, FP64 or FP32-mixed)
     served with continuous batching.  First all requests at once (saturated
-    request rate), then a Poisson stream at serve_load times that rate;
+    request rate), then a Poisson stream at serve_load times that rate, then
+    one at serve_overload times it (the same arrival gaps, rescaled);
     reports p50/p99 time-to-forecast and aggregate node-updates/s."""
     import torch
 
@@ -408,6 +447,11 @@ def run_serve(args):
     gaps = np.array([r["gap"] for r in reqs]) / rate
     arr = list(np.cumsum(gaps) - gaps[0])
     poi = serve(arr)
+    over = None
+    if args.serve_overload > 0:
+        scale = args.serve_load / args.serve_overload
+        over = serve([t * scale for t in arr])
+        over["load"] = args.serve_overload
     print(json.dumps({
         "metric": "ensemble time-to-forecast p50/p99 and aggregate node-updates/s", "unit": "s",
         "p50": poi["p50_s"], "p99": poi["p99_s"], "value": poi["node_updates_per_s"],
@@ -418,7 +462,7 @@ def run_serve(args):
                    "poisson_rate_per_s": rate, "load": args.serve_load,
                    "fp32_mixed_requests": sum(r["precision"] == "fp32_mixed" for r in reqs),
                    "total_node_updates": work},
-        "saturated": sat, "poisson": poi,
+        "saturated": sat, "poisson": poi, "overload": over,
     }))
 
 

@@ -68,6 +68,19 @@ enum numa_ic_kind { NUMA_IC_REST = 0, NUMA_IC_BUBBLE = 1, NUMA_IC_UNIFORM = 2, N
 /* Mesh, physics and precision.  Sec. 2.1 (order N, Lobatto points), Sec. 3
  * (the box and the cubed-sphere shell test cases), Sec. 4 (columns of
  * radial layers). */
+/* How the element kernel applies the metric terms of Eq. 5.
+ * AUTO: when every element's map to the reference cube is affine (a box with
+ *   warp = 0), the metric terms are constant over each element and the chain
+ *   rule commutes with the derivative, sum_c (dxi_d/dx_c) dF_c/dxi_d =
+ *   d/dxi_d (sum_c (dxi_d/dx_c) F_c); the kernel then differentiates the 15
+ *   contravariant fluxes instead of the 13 Cartesian flux components along
+ *   all three directions (15 contractions per node instead of 39, the same
+ *   operator up to rounding) and reads the metric terms once per element.
+ *   Any other mesh takes the per-node form.
+ * NODAL: always the per-node form of Eq. 5 (metric terms read at every node,
+ *   applied after the derivative). */
+typedef enum { NUMA_METRIC_AUTO = 0, NUMA_METRIC_NODAL = 1 } numa_metric_form;
+
 typedef struct {
   int mesh_kind;           /* numa_mesh_kind */
   int N;                   /* polynomial order, 1..8 (N+1 LGL points per direction) */
@@ -87,6 +100,7 @@ typedef struct {
   int ref_kind;            /* numa_ref_kind of the hydrostatic reference state */
   double theta0, T0;       /* isentropic potential temperature / isothermal temperature */
   int precision;           /* numa_precision */
+  int metric_form;         /* numa_metric_form: how the element kernel applies the metric terms */
 } numa_config;
 
 typedef struct {

@@ -227,6 +227,90 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
 // Field slots of the 13 unique flux components staged per element node.
 enum : int { kUx = 0, kUy, kUz, kTxx, kTxy, kTxz, kTyy, kTyz, kTzz, kPp, kHx, kHy, kHz, kNF };
 
+// Momentum and primitive fields of the global node behind element node n
+// (CG storage: gathered through l2g).
+template <typename T>
+struct NodeState {
+  T Ux, Uy, Uz, ux, uy, uz, th, pp;
+};
+
+template <typename T>
+__device__ __forceinline__ NodeState<T> gather_node(const VolumeArgs& a, long long n) {
+  const long long Ng = a.Ng;
+  const int g = a.l2g[n];
+  NodeState<T> z;
+  if constexpr (sizeof(T) == 8) {
+    const double* w = static_cast<const double*>(a.prim);
+    z.Ux = a.q[Ng + g];
+    z.Uy = a.q[2 * Ng + g];
+    z.Uz = a.q[3 * Ng + g];
+    z.ux = w[g];
+    z.uy = w[Ng + g];
+    z.uz = w[2 * Ng + g];
+    z.th = w[3 * Ng + g];
+    z.pp = w[4 * Ng + g];
+  } else {
+    const float* w = static_cast<const float*>(a.prim);
+    z.Ux = w[g];
+    z.Uy = w[Ng + g];
+    z.Uz = w[2 * Ng + g];
+    z.ux = w[3 * Ng + g];
+    z.uy = w[4 * Ng + g];
+    z.uz = w[5 * Ng + g];
+    z.th = w[6 * Ng + g];
+    z.pp = w[7 * Ng + g];
+  }
+  return z;
+}
+
+// The 13 unique flux components of element node l (index n) into the shared
+// tile F[kNF][NP]: F_rho = U, F_U = U (x) u + p' I (symmetric part stored
+// once), F_Theta = theta U.
+template <int N, typename T>
+__device__ __forceinline__ void stage_fluxes(const VolumeArgs& a, long long n, int l, T* F) {
+  constexpr int P = N + 1, NP = P * P * P;
+  const NodeState<T> z = gather_node<T>(a, n);
+  F[kUx * NP + l] = z.Ux;
+  F[kUy * NP + l] = z.Uy;
+  F[kUz * NP + l] = z.Uz;
+  F[kTxx * NP + l] = z.Ux * z.ux;
+  F[kTxy * NP + l] = z.Ux * z.uy;
+  F[kTxz * NP + l] = z.Ux * z.uz;
+  F[kTyy * NP + l] = z.Uy * z.uy;
+  F[kTyz * NP + l] = z.Uy * z.uz;
+  F[kTzz * NP + l] = z.Uz * z.uz;
+  F[kPp * NP + l] = z.pp;
+  F[kHx * NP + l] = z.th * z.Ux;
+  F[kHy * NP + l] = z.th * z.Uy;
+  F[kHz * NP + l] = z.th * z.Uz;
+}
+
+// Affine elements (every element of a box without warp) have the same metric
+// terms B[3d+c] = d xi_d / d x_c at all their nodes, so the chain rule of
+// Eq. 5 commutes with the derivative:
+//   sum_c B_dc dF_vc/d xi_d = d/d xi_d (sum_c B_dc F_vc).
+// Node l stages the contravariant fluxes G[3v+d] = sum_c B_dc F_vc of the
+// five equations v along the three directions d (15 values):
+//   mass      G = B_d . U
+//   momentum  G_x = U_x (B_d . u) + B_dx p'   (and y, z)
+//   Theta     G = theta (B_d . U)
+template <int N, typename T>
+__device__ __forceinline__ void stage_fluxes_affine(const VolumeArgs& a, long long n, int l, const T (&B)[9], T* G) {
+  constexpr int P = N + 1, NP = P * P * P;
+  const NodeState<T> z = gather_node<T>(a, n);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T b0 = B[3 * d], b1 = B[3 * d + 1], b2 = B[3 * d + 2];
+    const T ud = fma(b0, z.ux, fma(b1, z.uy, b2 * z.uz));
+    const T Gr = fma(b0, z.Ux, fma(b1, z.Uy, b2 * z.Uz));
+    G[d * NP + l] = Gr;
+    G[(3 + d) * NP + l] = fma(z.Ux, ud, b0 * z.pp);
+    G[(6 + d) * NP + l] = fma(z.Uy, ud, b1 * z.pp);
+    G[(9 + d) * NP + l] = fma(z.Uz, ud, b2 * z.pp);
+    G[(12 + d) * NP + l] = z.th * Gr;
+  }
+}
+
 // create_rhs of element e of one mesh, by the whole CTA (one thread per
 // element node); smem_raw holds kNF*(N+1)^3 + (N+1)^2 values of T.  Shared by
 // the single-mesh kernel and the ragged multi-member kernel, so that a member
@@ -248,47 +332,8 @@ __device__ __forceinline__ void volume_element(const VolumeArgs& a, long long e,
   const int l = threadIdx.x;
   for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
   const long long n = (long long)e * NP + l;
-  const long long Ng = a.Ng, Nl = a.Nl;
-  if (l < NP) {
-    // gather this node's momentum and primitive fields (CG storage)
-    const int g = a.l2g[n];
-    T Ux, Uy, Uz, ux, uy, uz, th, pp;
-    if constexpr (sizeof(T) == 8) {
-      const double* w = static_cast<const double*>(a.prim);
-      Ux = a.q[Ng + g];
-      Uy = a.q[2 * Ng + g];
-      Uz = a.q[3 * Ng + g];
-      ux = w[g];
-      uy = w[Ng + g];
-      uz = w[2 * Ng + g];
-      th = w[3 * Ng + g];
-      pp = w[4 * Ng + g];
-    } else {
-      const float* w = static_cast<const float*>(a.prim);
-      Ux = w[g];
-      Uy = w[Ng + g];
-      Uz = w[2 * Ng + g];
-      ux = w[3 * Ng + g];
-      uy = w[4 * Ng + g];
-      uz = w[5 * Ng + g];
-      th = w[6 * Ng + g];
-      pp = w[7 * Ng + g];
-    }
-    // F_rho = U, F_U = U (x) u + p' I (symmetric part stored once), F_Theta = theta U
-    F[kUx * NP + l] = Ux;
-    F[kUy * NP + l] = Uy;
-    F[kUz * NP + l] = Uz;
-    F[kTxx * NP + l] = Ux * ux;
-    F[kTxy * NP + l] = Ux * uy;
-    F[kTxz * NP + l] = Ux * uz;
-    F[kTyy * NP + l] = Uy * uy;
-    F[kTyz * NP + l] = Uy * uz;
-    F[kTzz * NP + l] = Uz * uz;
-    F[kPp * NP + l] = pp;
-    F[kHx * NP + l] = th * Ux;
-    F[kHy * NP + l] = th * Uy;
-    F[kHz * NP + l] = th * Uz;
-  }
+  const long long Nl = a.Nl;
+  if (l < NP) stage_fluxes<N, T>(a, n, l, F);
   __syncthreads();
   if (l >= NP) return;
   const int i = l % P, j = (l / P) % P, k = l / (P * P);
@@ -343,6 +388,237 @@ __device__ __forceinline__ void volume_element(const VolumeArgs& a, long long e,
   re[2 * Nl + n] = -(jw * div_y);
   re[3 * Nl + n] = -(jw * div_z);
   re[4 * Nl + n] = -(jw * div_t);
+}
+
+// create_rhs of an affine element (see stage_fluxes_affine), one thread per
+// element node: each equation's divergence is three contractions with D of
+// the staged contravariant fluxes, 15 per node instead of 39.  The element's
+// metric terms are read at its first node.  smem_raw holds 15 (N+1)^3 +
+// (N+1)^2 values of T.
+template <int N, typename T>
+__device__ __forceinline__ void volume_element_affine(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  T* G = reinterpret_cast<T*>(smem_raw);  // [15][NP]
+  T* Ds = G + 15 * NP;                      // [P][P]
+  const T* Dg = reinterpret_cast<const T*>(a.D64);
+  const T* met = reinterpret_cast<const T*>(a.met64);
+  static_assert(sizeof(T) == 8, "FP64 form");
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
+  const long long Nl = a.Nl, e0 = (long long)e * NP, n = e0 + l;
+  if (l < NP) {
+    T B[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + e0];
+    stage_fluxes_affine<N, T>(a, n, l, B, G);
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  T dx[P], dy[P], dz[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    dx[m] = Ds[i * P + m];
+    dy[m] = Ds[j * P + m];
+    dz[m] = Ds[k * P + m];
+  }
+  const T jw = met[9 * Nl + n];
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  T* re = static_cast<T*>(a.re);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const T* g0 = G + (3 * v) * NP;
+    const T* g1 = g0 + NP;
+    const T* g2 = g1 + NP;
+    T t = T(0);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dx[m], g0[bx + m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dy[m], g1[by + P * m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dz[m], g2[bz + P * P * m], t);
+    re[v * Nl + n] = -(jw * t);
+  }
+}
+
+// D of every order N = 1..8 in FP32 ([N][(N+1)^2], row-major), read by the
+// FP32 line kernel as instruction operands.  Written at bind time; every
+// mesh of one order writes the same values.
+__constant__ float c_D32[9 * 81];
+
+template <int N>
+__device__ __forceinline__ float cD32(int i, int m) {
+  return c_D32[N * 81 + i * (N + 1) + m];
+}
+
+// Directions of the line kernel: lines of one direction per work group of
+// W threads (whole warps when three of them fit in the CTA, so that each
+// warp reads one direction's lines without conflicts between directions).
+template <int N>
+__host__ __device__ constexpr int line_group() {
+  constexpr int P2 = (N + 1) * (N + 1), NT = ((N + 1) * P2 + 31) / 32 * 32, W32 = (P2 + 31) / 32 * 32;
+  return 3 * W32 <= NT ? W32 : P2;
+}
+
+// create_rhs of element e in the FP32 form, organised by 1D lines of nodes
+// (Eq. 5 is a contraction along xi, eta and zeta).  Thread t < 3W takes one
+// line along one reference direction d; for each field it reads the line's
+// N+1 values once (distinct addresses, no broadcast) and applies the whole
+// of D to them.
+//   general element: the 13 flux fields, each derivative folded into the
+//     divergence of its equation at the line's nodes with row d of the
+//     metric (d xi_d / d x_c, read before the barrier);
+//   affine element (AFF): the 5 contravariant fluxes G[3v+d] of direction d
+//     (stage_fluxes_affine), whose derivatives are the partial sums.
+// The partial sums go to shared memory over the no longer needed flux tile;
+// one thread per element node then adds the three directions and weights by
+// -Jw.  Shared memory: 15 (N+1)^3 floats.
+template <int N, bool AFF>
+__device__ __forceinline__ void volume_element_lines(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, P2 = P * P, NP = P2 * P;
+  constexpr int W = line_group<N>();
+  static_assert(3 * W <= (NP + 31) / 32 * 32, "one line per thread");
+  float* F = reinterpret_cast<float*>(smem_raw);  // [kNF or 15][NP], then [3][5][NP]
+  const float* met = a.met32;
+  const long long Nl = a.Nl, e0 = (long long)e * NP;
+  const int l = threadIdx.x;
+  const int d = l / W, r = l - (l / W) * W;
+  const bool act = d < 3 && r < P2;
+  int base = 0, stride = 0;
+  if (d == 0) {  // along xi: line (j, k)
+    base = P * r;
+    stride = 1;
+  } else if (d == 1) {  // along eta: line (i, k)
+    base = r % P + P2 * (r / P);
+    stride = P;
+  } else {  // along zeta: line (i, j)
+    base = r;
+    stride = P2;
+  }
+  float part[5][P];
+  if constexpr (AFF) {
+    if (l < NP) {
+      float B[9];  // the element's metric terms, at its first node
+#pragma unroll
+      for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + e0];
+      stage_fluxes_affine<N, float>(a, e0 + l, l, B, F);
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float* Gv = F + (3 * v + d) * NP + base;
+        float x[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) x[m] = Gv[m * stride];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          float t = 0.0f;
+#pragma unroll
+          for (int m = 0; m < P; ++m) t = fmaf(cD32<N>(p, m), x[m], t);
+          part[v][p] = t;
+        }
+      }
+    }
+  } else {
+    float B[3][P];  // d xi_d / d x_c at the line's nodes
+    if (act) {
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) B[c][p] = met[(3 * d + c) * Nl + e0 + base + p * stride];
+    }
+    if (l < NP) stage_fluxes<N, float>(a, e0 + l, l, F);
+    __syncthreads();
+    if (act) {
+      // s[p] = d F_f / d xi_d at node p of the line
+      auto deriv = [&](int f, float (&s)[P]) {
+        const float* Ff = F + f * NP + base;
+        float x[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) x[m] = Ff[m * stride];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          float t = 0.0f;
+#pragma unroll
+          for (int m = 0; m < P; ++m) t = fmaf(cD32<N>(p, m), x[m], t);
+          s[p] = t;
+        }
+      };
+      float s[P];
+      // mass: div U
+      deriv(kUx, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[0][p] = s[p] * B[0][p];
+      deriv(kUy, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[0][p] = fmaf(s[p], B[1][p], part[0][p]);
+      deriv(kUz, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[0][p] = fmaf(s[p], B[2][p], part[0][p]);
+      // momentum: div (U (x) u + p' I)
+      deriv(kPp, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        part[1][p] = s[p] * B[0][p];
+        part[2][p] = s[p] * B[1][p];
+        part[3][p] = s[p] * B[2][p];
+      }
+      deriv(kTxx, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[1][p] = fmaf(s[p], B[0][p], part[1][p]);
+      deriv(kTxy, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        part[1][p] = fmaf(s[p], B[1][p], part[1][p]);
+        part[2][p] = fmaf(s[p], B[0][p], part[2][p]);
+      }
+      deriv(kTxz, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        part[1][p] = fmaf(s[p], B[2][p], part[1][p]);
+        part[3][p] = fmaf(s[p], B[0][p], part[3][p]);
+      }
+      deriv(kTyy, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[2][p] = fmaf(s[p], B[1][p], part[2][p]);
+      deriv(kTyz, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        part[2][p] = fmaf(s[p], B[2][p], part[2][p]);
+        part[3][p] = fmaf(s[p], B[1][p], part[3][p]);
+      }
+      deriv(kTzz, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[3][p] = fmaf(s[p], B[2][p], part[3][p]);
+      // potential temperature: div (theta U)
+      deriv(kHx, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[4][p] = s[p] * B[0][p];
+      deriv(kHy, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[4][p] = fmaf(s[p], B[1][p], part[4][p]);
+      deriv(kHz, s);
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[4][p] = fmaf(s[p], B[2][p], part[4][p]);
+    }
+  }
+  __syncthreads();  // every flux value has been read: the tile now takes the partial sums
+  if (act) {
+    float* acc = F + d * 5 * NP + base;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int p = 0; p < P; ++p) acc[v * NP + p * stride] = part[v][p];
+  }
+  __syncthreads();
+  if (l < NP) {
+    const long long n = e0 + l;
+    const float jw = met[9 * Nl + n];
+    float* re = static_cast<float*>(a.re);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) re[v * Nl + n] = -(jw * ((F[v * NP + l] + F[(5 + v) * NP + l]) + F[(10 + v) * NP + l]));
+  }
 }
 
 // create_rhs of element e in the pairs mode: the same steps as
@@ -456,23 +732,29 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
 
 // Dynamic shared memory of one element: the staged fluxes, D and (pairs
 // mode) the node-0 base values.
-template <int N, typename T>
+template <int N, typename T, bool AFF>
 constexpr size_t element_smem_bytes() {
   constexpr int P = N + 1, NP = P * P * P;
+  if constexpr (std::is_same<T, float>::value) return sizeof(float) * (kNF > 15 ? kNF : 15) * NP;
+  if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (15 * NP + P * P);
   return sizeof(T) * (kNF * NP + P * P + kNF);
 }
 
-template <int N, typename T>
+// Element kernel of one precision; AFF selects the affine-element form
+// (FP64 and FP32; the pairs mode has only the general form).
+template <int N, typename T, bool AFF>
 __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   if constexpr (std::is_same<T, Pairs>::value) volume_element_pairs<N>(a, e, smem_raw);
+  else if constexpr (std::is_same<T, float>::value) volume_element_lines<N, AFF>(a, e, smem_raw);
+  else if constexpr (AFF) volume_element_affine<N, T>(a, e, smem_raw);
   else volume_element<N, T>(a, e, smem_raw);
 }
 
-template <int N, typename T>
+template <int N, typename T, bool AFF>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     volume_kernel(VolumeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  element_rhs<N, T>(a, blockIdx.x, smem_raw);
+  element_rhs<N, T, AFF>(a, blockIdx.x, smem_raw);
 }
 
 template <typename RT>
@@ -593,7 +875,7 @@ __device__ __forceinline__ int ragged_find(const long long* prefix, int n, long 
   return lo;
 }
 
-template <int N, typename T>
+template <int N, typename T, bool AFF>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     volume_ragged(const MemberDesc* __restrict__ d, const RaggedGroup* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -610,7 +892,7 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     __syncthreads();
     // (uniform across the CTA) guard against a table that disagrees with the member
     if (s_m >= 0 && s_m < kMaxMembers && s_e >= 0 && s_e < d[s_m].va.Ne)
-      element_rhs<N, T>(d[s_m].va, s_e, smem_raw);
+      element_rhs<N, T, AFF>(d[s_m].va, s_e, smem_raw);
     __syncthreads();
   }
 }
@@ -630,33 +912,34 @@ __global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restric
   }
 }
 
-template <int N, typename T>
+template <int N, typename T, bool AFF>
 cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = element_smem_bytes<N, T>();
+  const size_t smem = element_smem_bytes<N, T, AFF>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(volume_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(volume_kernel<N, T, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   if (a.Ne == 0) return cudaSuccess;
-  volume_kernel<N, T><<<a.Ne, NT, smem, s>>>(a);
+  volume_kernel<N, T, AFF><<<a.Ne, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool AFF>
 cudaError_t launch_volume_p(int N, const VolumeArgs& a, cudaStream_t s) {
   switch (N) {
-    case 1: return launch_volume_t<1, T>(a, s);
-    case 2: return launch_volume_t<2, T>(a, s);
-    case 3: return launch_volume_t<3, T>(a, s);
-    case 4: return launch_volume_t<4, T>(a, s);
-    case 5: return launch_volume_t<5, T>(a, s);
-    case 6: return launch_volume_t<6, T>(a, s);
-    case 7: return launch_volume_t<7, T>(a, s);
-    case 8: return launch_volume_t<8, T>(a, s);
+    case 1: return launch_volume_t<1, T, AFF>(a, s);
+    case 2: return launch_volume_t<2, T, AFF>(a, s);
+    case 3: return launch_volume_t<3, T, AFF>(a, s);
+    case 4: return launch_volume_t<4, T, AFF>(a, s);
+    case 5: return launch_volume_t<5, T, AFF>(a, s);
+    case 6: return launch_volume_t<6, T, AFF>(a, s);
+    case 7: return launch_volume_t<7, T, AFF>(a, s);
+    case 8: return launch_volume_t<8, T, AFF>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -669,6 +952,12 @@ void launch_update_m(const UpdateArgs& a, unsigned nb, int nt, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t upload_d32_constant(int N, const float* D, cudaStream_t s) {
+  if (N < 1 || N > 8) return cudaErrorInvalidValue;
+  return cudaMemcpyToSymbolAsync(c_D32, D, sizeof(float) * (N + 1) * (N + 1), sizeof(float) * 81 * N,
+                                 cudaMemcpyHostToDevice, s);
+}
+
 cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
   if (a.Ng == 0) return cudaSuccess;
   const int nt = 256;
@@ -677,9 +966,10 @@ cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
-  if (precision == NUMA_FP32_MIXED) return launch_volume_p<float>(N, a, s);
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_p<Pairs>(N, a, s);
-  return launch_volume_p<double>(N, a, s);
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_p<Pairs, false>(N, a, s);
+  if (precision == NUMA_FP32_MIXED)
+    return a.affine ? launch_volume_p<float, true>(N, a, s) : launch_volume_p<float, false>(N, a, s);
+  return a.affine ? launch_volume_p<double, true>(N, a, s) : launch_volume_p<double, false>(N, a, s);
 }
 
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
@@ -713,45 +1003,48 @@ int sm_count() {
 }
 
 // Persistent launch: as many CTAs as fit on the GPU at once.
-template <int N, typename T>
+template <int N, typename T, bool AFF>
 cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
-  const size_t smem = element_smem_bytes<N, T>();
+  const size_t smem = element_smem_bytes<N, T, AFF>();
   static int grid = 0;
   if (!grid) {
-    cudaError_t e = cudaFuncSetAttribute(volume_ragged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(volume_ragged<N, T, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, volume_ragged<N, T>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, volume_ragged<N, T, AFF>, NT, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * sm_count();
   }
-  volume_ragged<N, T><<<grid, NT, smem, s>>>(d, g);
+  volume_ragged<N, T, AFF><<<grid, NT, smem, s>>>(d, g);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool AFF>
 cudaError_t launch_volume_ragged_p(int N, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
   switch (N) {
-    case 1: return launch_volume_ragged_t<1, T>(d, g, s);
-    case 2: return launch_volume_ragged_t<2, T>(d, g, s);
-    case 3: return launch_volume_ragged_t<3, T>(d, g, s);
-    case 4: return launch_volume_ragged_t<4, T>(d, g, s);
-    case 5: return launch_volume_ragged_t<5, T>(d, g, s);
-    case 6: return launch_volume_ragged_t<6, T>(d, g, s);
-    case 7: return launch_volume_ragged_t<7, T>(d, g, s);
-    case 8: return launch_volume_ragged_t<8, T>(d, g, s);
+    case 1: return launch_volume_ragged_t<1, T, AFF>(d, g, s);
+    case 2: return launch_volume_ragged_t<2, T, AFF>(d, g, s);
+    case 3: return launch_volume_ragged_t<3, T, AFF>(d, g, s);
+    case 4: return launch_volume_ragged_t<4, T, AFF>(d, g, s);
+    case 5: return launch_volume_ragged_t<5, T, AFF>(d, g, s);
+    case 6: return launch_volume_ragged_t<6, T, AFF>(d, g, s);
+    case 7: return launch_volume_ragged_t<7, T, AFF>(d, g, s);
+    case 8: return launch_volume_ragged_t<8, T, AFF>(d, g, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_volume_ragged(int N, int precision, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s) {
-  if (precision == NUMA_FP32_MIXED) return launch_volume_ragged_p<float>(N, d, g, s);
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_p<Pairs>(N, d, g, s);
-  return launch_volume_ragged_p<double>(N, d, g, s);
+cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s) {
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_p<Pairs, false>(N, d, g, s);
+  if (precision == NUMA_FP32_MIXED)
+    return affine ? launch_volume_ragged_p<float, true>(N, d, g, s) : launch_volume_ragged_p<float, false>(N, d, g, s);
+  return affine ? launch_volume_ragged_p<double, true>(N, d, g, s) : launch_volume_ragged_p<double, false>(N, d, g, s);
 }
 
 cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,

@@ -61,6 +61,7 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
+  a.affine = affine_elements(c->cfg) ? 1 : 0;
   return a;
 }
 
@@ -205,6 +206,7 @@ int numa_create(const numa_config* cfg, numa_ctx** out) {
   if (!cfg) return NUMA_EINVAL;
   if (cfg->precision != NUMA_FP64 && cfg->precision != NUMA_FP32_MIXED && cfg->precision != NUMA_FP64_PAIRS)
     return NUMA_EINVAL;
+  if (cfg->metric_form != NUMA_METRIC_AUTO && cfg->metric_form != NUMA_METRIC_NODAL) return NUMA_EINVAL;
   if (!(cfg->cv > 0) || !(cfg->cp > cfg->cv) || !(cfg->Rd > 0) || !(cfg->P00 > 0)) return NUMA_EINVAL;
   numa_ctx* c = new (std::nothrow) numa_ctx();
   if (!c) return NUMA_ENOMEM;
@@ -282,6 +284,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.D64, m.D.data(), m.D.size() * 8);
   up(L.D32, D32.data(), D32.size() * 4);
   up(L.D2, D2.data(), D2.size() * 4);
+  if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
   up(L.csr_idx, m.csr_idx.data(), Nl * 4);

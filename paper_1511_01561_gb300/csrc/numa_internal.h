@@ -87,6 +87,12 @@ struct PrimArgs {
   double eos[kEosTerms];  // binomial coefficients C(gamma, k), k = 1..kEosTerms
 };
 
+// Every element of the mesh maps affinely onto the reference cube (a box
+// without warp) and the configuration lets the kernel use that.
+inline bool affine_elements(const numa_config& c) {
+  return c.mesh_kind == NUMA_MESH_BOX && c.warp == 0.0 && c.metric_form == NUMA_METRIC_AUTO;
+}
+
 struct VolumeArgs {
   const double* q;     // state [5][Ng] (FP64 mode reads U from it)
   const void* prim;    // primitive fields of q
@@ -100,6 +106,7 @@ struct VolumeArgs {
   void* re;            // [5][Nl] output
   long long Ng, Nl;
   int Ne;
+  int affine;          // 1: every element is affine, the kernel takes the contravariant-flux form
 };
 
 struct UpdateArgs {
@@ -125,6 +132,9 @@ struct UpdateArgs {
 };
 
 cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s);
+// Copies D of order N (FP32, (N+1)^2 values, host memory that stays valid
+// until s has run the copy) into the constant table of the FP32 line kernel.
+cudaError_t upload_d32_constant(int N, const float* D, cudaStream_t s);
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s);
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 
@@ -149,7 +159,8 @@ struct RaggedGroup {
   int member[kMaxMembers];
 };
 
-cudaError_t launch_volume_ragged(int N, int precision, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s);
+cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s);
 cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
                                  cudaStream_t s);
 

@@ -98,7 +98,7 @@ struct Request {
   std::string err;
 };
 
-using GroupKey = std::tuple<int, int, int>;  // N, precision, mesh kind
+using GroupKey = std::tuple<int, int, int, int>;  // N, precision, mesh kind, affine elements
 
 // Workspace bytes of a configuration without building its mesh.
 bool workspace_bytes_of(const numa_config& c, size_t* bytes, long long* Ng) {
@@ -222,7 +222,7 @@ void rebuild_tables(numa_sched* s) {
   for (int g = 0; g < kMaxGroups; ++g) s->h_groups[g].n = 0;
   for (long long id : s->active) {
     Request& r = *s->reqs[id];
-    GroupKey k{r.cfg.N, r.cfg.precision, r.cfg.mesh_kind};
+    GroupKey k{r.cfg.N, r.cfg.precision, r.cfg.mesh_kind, affine_elements(r.cfg) ? 1 : 0};
     auto it = gi.find(k);
     int g;
     if (it == gi.end()) {
@@ -251,9 +251,10 @@ cudaError_t enqueue_step(numa_sched* s, cudaStream_t st) {
   for (size_t g = 0; g < s->groups.size(); ++g) {
     const int N = std::get<0>(s->groups[g]), prec = std::get<1>(s->groups[g]);
     const bool shell = std::get<2>(s->groups[g]) == NUMA_MESH_SHELL;
+    const bool affine = std::get<3>(s->groups[g]) != 0;
     for (int stage = 0; stage < 3; ++stage) {
       const MemberDesc* d = s->d_desc + (size_t)stage * kMaxMembers;
-      cudaError_t e = launch_volume_ragged(N, prec, d, s->d_groups + g, st);
+      cudaError_t e = launch_volume_ragged(N, prec, affine, d, s->d_groups + g, st);
       if (e == cudaSuccess) e = launch_update_ragged(prec, shell, stage, d, s->d_groups + g, st);
       if (e != cudaSuccess) return e;
     }

@@ -20,6 +20,7 @@ ERRORS = {-1: "NUMA_EINVAL", -2: "NUMA_ENOMEM", -3: "NUMA_ECUDA", -4: "NUMA_ENON
           -5: "NUMA_ETIMEOUT", -6: "NUMA_EBUDGET", -7: "NUMA_ESTATE"}
 MESH = {"box": 0, "shell": 1}
 REF = {"isentropic": 0, "isothermal": 1}
+METRIC_FORM = {"auto": 0, "nodal": 1}
 PRECISION = {"fp64": 0, "fp32_mixed": 1, "fp64_pairs": 2}
 IC = {"rest": 0, "bubble": 1, "uniform": 2, "jetwave": 3}
 
@@ -41,7 +42,7 @@ class numa_config(ctypes.Structure):
         ("Rd", ctypes.c_double), ("cp", ctypes.c_double), ("cv", ctypes.c_double),
         ("P00", ctypes.c_double), ("g", ctypes.c_double), ("Omega", ctypes.c_double),
         ("ref_kind", ctypes.c_int), ("theta0", ctypes.c_double), ("T0", ctypes.c_double),
-        ("precision", ctypes.c_int),
+        ("precision", ctypes.c_int), ("metric_form", ctypes.c_int),
     ]
 
 
@@ -119,6 +120,7 @@ def make_config(cfg: dict, precision: str = "fp64") -> numa_config:
     c.theta0 = float(cfg.get("theta0", 300.0))
     c.T0 = float(cfg.get("T0", 300.0))
     c.precision = PRECISION[cfg.get("precision", precision)]
+    c.metric_form = METRIC_FORM[cfg.get("metric_form", "auto")]
     return c
 
 

@@ -37,6 +37,7 @@ def _dx_min(cfg, orc_mesh):
 
 
 def _gpu_rhs(numa, cfg, q, precision="fp64"):
+    """RHS through the C ABI, twice (the two results must agree bit for bit)."""
     s = numa.Solver(cfg, precision)
     try:
         R = s.rhs(q).cpu().numpy()
@@ -93,6 +94,25 @@ def test_rhs_parity_box(numa, orc, name, cfg, kind, precision):
     assert err.max() <= TOL_RHS, err
 
 
+# Boxes without warp take the affine-element (contravariant flux) kernel by
+# default; the per-node form of Eq. 5 is held to the same bars on them.
+NODAL_CASES = [c for c in BOX_CASES if c[1].get("warp", 0.0) == 0.0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("name,cfg,kind", NODAL_CASES, ids=[c[0] for c in NODAL_CASES])
+def test_rhs_parity_box_nodal_form(numa, orc, name, cfg, kind, precision):
+    m = orc.Mesh(cfg)
+    q = _state(m, cfg, kind, seed=zlib.crc32(name.encode()) % 1000)
+    Ro = m.rhs(q)
+    Rg, _ = _gpu_rhs(numa, dict(cfg, metric_form="nodal"), q, precision)
+    err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
+    if precision == "fp64":
+        assert err.max() <= TOL_RHS, err
+    else:
+        assert err[:, 0].max() <= TOL_FP32_RHS, err
+
+
 @pytest.mark.parametrize("precision", FP64_MODES)
 @pytest.mark.parametrize("cfg", [I.shell(2, 2, 4), I.shell(3, 1, 3), I.shell(1, 2, 6, Omega=0.0)])
 def test_rhs_parity_shell(numa, orc, cfg, precision):
@@ -138,12 +158,12 @@ def test_init_state_parity(numa, orc):
     assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
 
 
-@pytest.mark.parametrize("precision", FP64_MODES)
-def test_rk3_100_steps_bubble(numa, orc, precision):
+@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal")])
+def test_rk3_100_steps_bubble(numa, orc, precision, form):
     """Workload bubble_4x4x4_N4: 100 SSP-RK3 steps at dt = 0.01 s."""
     w = I.WORKLOADS["bubble_4x4x4_N4"]
-    cfg = w["cfg"]
-    m = orc.Mesh(cfg)
+    cfg = dict(w["cfg"], metric_form=form)
+    m = orc.Mesh(w["cfg"])
     q0 = m.init_state(*w["ic"])
     qo = m.run(q0, w["dt"], w["steps"])
     s = numa.Solver(cfg, precision)
@@ -195,10 +215,10 @@ def test_full_size_bubble_rhs(numa, orc):
     q = m.init_state("bubble", I.BUBBLE_PARAMS) + 0.1 * _state(m, cfg, "smooth", seed=21)
     Ro = m.rhs(q)
     floors = rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max())
-    for precision in FP64_MODES:
-        Rg, _ = _gpu_rhs(numa, cfg, q, precision)
+    for precision, form in (("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal")):
+        Rg, _ = _gpu_rhs(numa, dict(cfg, metric_form=form), q, precision)
         err = rel_errors(Rg, Ro, floors)
-        assert err.max() <= TOL_RHS, (precision, err)
+        assert err.max() <= TOL_RHS, (precision, form, err)
 
 
 def test_nonfinite_flag_and_errors(numa):
@@ -231,13 +251,29 @@ def test_nonfinite_flag_and_errors(numa):
 TOL_FP32_RHS = 2e-5
 
 
-@pytest.mark.parametrize("name,cfg,kind", BOX_CASES[:5], ids=[c[0] for c in BOX_CASES[:5]])
+@pytest.mark.parametrize("name,cfg,kind", BOX_CASES, ids=[c[0] for c in BOX_CASES])
 def test_fp32_mixed_rhs_error(numa, orc, name, cfg, kind):
     m = orc.Mesh(cfg)
     q = _state(m, cfg, kind, seed=31)
     Ro = m.rhs(q)
     Rg, _ = _gpu_rhs(numa, cfg, q, "fp32_mixed")
     err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
+    assert err[:, 0].max() <= TOL_FP32_RHS, err
+
+
+@pytest.mark.parametrize("cfg", [I.shell(2, 2, 4), I.shell(1, 2, 6, Omega=0.0)])
+def test_fp32_mixed_rhs_error_shell(numa, orc, cfg):
+    m = orc.Mesh(cfg)
+    q = _state(m, cfg, "smooth", seed=5) + 0.1 * _state(m, cfg, "random", seed=6)
+    Ro = m.rhs(q)
+    s = numa.Solver(cfg, "fp32_mixed")
+    try:
+        perm = match_nodes(s.coords(), m.coords(), tol=1e-3)
+        Rg = s.rhs(np.ascontiguousarray(q[:, perm])).cpu().numpy()
+    finally:
+        s.close()
+    Rref = Ro[:, perm]
+    err = rel_errors(Rg, Rref, rhs_floors(Rref, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
     assert err[:, 0].max() <= TOL_FP32_RHS, err
 
 
