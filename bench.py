@@ -69,18 +69,24 @@ FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
-# source they were taken on (first 16 hex digits of its sha256).
-NCU_TRAFFIC = {"kernels_sha256_16": "360368949e549b56",
-               "volume_fp64": 481.620992e6 + 143.209472e6,
-               "volume_fp32": 248.970240e6 + 64.139008e6,
-               "volume_pairs": 481.579520e6 + 142.462208e6}
+# sources they were taken on (first 16 hex digits of the sha256 of the kernel
+# sources, see kernel_source_hash).
+NCU_TRAFFIC = {"kernels_sha256_16": None}
+
+KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1511_01561_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(key: str):
-    import hashlib
-    with open(os.path.join(ROOT, "paper_1511_01561_gb300", "csrc", "kernels.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return NCU_TRAFFIC.get(key) if sha == NCU_TRAFFIC["kernels_sha256_16"] else None
+    return NCU_TRAFFIC.get(key) if kernel_source_hash() == NCU_TRAFFIC["kernels_sha256_16"] else None
 
 
 def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:

@@ -1,18 +1,16 @@
-// CUDA kernels of the GB300 NUMA hot path (sm_103a):
-//   prim_kernel   : per global node, the primitive fields (u, theta, p') the
-//                   element kernel differentiates fluxes of;
-//   volume_kernel : per-element create_rhs of Eq. 4 / Eq. 5 (fluxes, tensor-
-//                   product derivatives with D, chain rule with the metric
-//                   terms, -Jw div F), one CTA per element, flux fields
-//                   staged in shared memory;
-//   update_kernel : per global node, deterministic direct stiffness
-//                   summation over a precomputed inverse map (fixed order, no
-//                   atomics), inverse mass matrix, sources, wall condition,
-//                   the SSP-RK3 stage combination, and the primitive fields of
-//                   the new stage state.
+// Device code shared by the kernel translation units of the GB300 NUMA hot
+// path (sm_103a): FP64-pipe-free conversions, float-pair arithmetic, the
+// equation of state, the element kernels of Eq. 4 / Eq. 5 (per-node, affine
+// and line forms), the per-node DSS / inverse-mass / RK-stage update, the
+// ragged multi-member kernels, and their launch templates.  Everything is in
+// an anonymous namespace: each translation unit instantiates the templates
+// it launches.
+//
 // GB300 executes FP64 at 1/64 of the FP32 rate, so everything that does not
 // need FP64 stays off the FP64 pipe: float<->double conversions and the
 // finiteness test are done with integer operations on the bit patterns.
+#pragma once
+
 #include <cstdint>
 #include <type_traits>
 
@@ -165,10 +163,10 @@ __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
 }
 
 __device__ __forceinline__ float eos_ratio_f(float x, const PrimArgs& a) {
-  if (fabsf(x) > 0.03125f) return eos_ratio_f_rare(x, (float)a.gamma);
-  float t = (float)a.eos[6];
+  if (fabsf(x) > 0.03125f) return eos_ratio_f_rare(x, a.gammaf);
+  float t = a.eosf[6];
 #pragma unroll
-  for (int k = 5; k >= 0; --k) t = fmaf(t, x, (float)a.eos[k]);
+  for (int k = 5; k >= 0; --k) t = fmaf(t, x, a.eosf[k]);
   return t * x;
 }
 
@@ -217,12 +215,6 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
   }
 }
 
-__global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
-  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= a.Ng) return;
-  const long long Ng = a.Ng;
-  write_prim(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
-}
 
 // Field slots of the 13 unique flux components staged per element node.
 enum : int { kUx = 0, kUy, kUz, kTxx, kTxy, kTxz, kTyy, kTyz, kTzz, kPp, kHx, kHy, kHz, kNF };
@@ -944,53 +936,7 @@ cudaError_t launch_volume_p(int N, const VolumeArgs& a, cudaStream_t s) {
   }
 }
 
-template <int MODE, typename RT>
-void launch_update_m(const UpdateArgs& a, unsigned nb, int nt, cudaStream_t s) {
-  if (a.gvec) update_kernel<MODE, true, RT><<<nb, nt, 0, s>>>(a);
-  else update_kernel<MODE, false, RT><<<nb, nt, 0, s>>>(a);
-}
 
-}  // namespace
-
-cudaError_t upload_d32_constant(int N, const float* D, cudaStream_t s) {
-  if (N < 1 || N > 8) return cudaErrorInvalidValue;
-  return cudaMemcpyToSymbolAsync(c_D32, D, sizeof(float) * (N + 1) * (N + 1), sizeof(float) * 81 * N,
-                                 cudaMemcpyHostToDevice, s);
-}
-
-cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
-  if (a.Ng == 0) return cudaSuccess;
-  const int nt = 256;
-  prim_kernel<<<(unsigned)((a.Ng + nt - 1) / nt), nt, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_p<Pairs, false>(N, a, s);
-  if (precision == NUMA_FP32_MIXED)
-    return a.affine ? launch_volume_p<float, true>(N, a, s) : launch_volume_p<float, false>(N, a, s);
-  return a.affine ? launch_volume_p<double, true>(N, a, s) : launch_volume_p<double, false>(N, a, s);
-}
-
-cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
-  if (a.Ng == 0) return cudaSuccess;
-  const int nt = 256;
-  const unsigned nb = (unsigned)((a.Ng + nt - 1) / nt);
-  const bool f32 = precision == NUMA_FP32_MIXED;
-  if (a.mode == 0) {
-    if (f32) launch_update_m<0, float>(a, nb, nt, s);
-    else launch_update_m<0, double>(a, nb, nt, s);
-  } else if (a.first_stage) {
-    if (f32) launch_update_m<2, float>(a, nb, nt, s);
-    else launch_update_m<2, double>(a, nb, nt, s);
-  } else {
-    if (f32) launch_update_m<1, float>(a, nb, nt, s);
-    else launch_update_m<1, double>(a, nb, nt, s);
-  }
-  return cudaGetLastError();
-}
-
-namespace {
 
 int sm_count() {
   static int n = 0;
@@ -1038,33 +984,4 @@ cudaError_t launch_volume_ragged_p(int N, const MemberDesc* d, const RaggedGroup
 }
 
 }  // namespace
-
-cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
-                                 cudaStream_t s) {
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_p<Pairs, false>(N, d, g, s);
-  if (precision == NUMA_FP32_MIXED)
-    return affine ? launch_volume_ragged_p<float, true>(N, d, g, s) : launch_volume_ragged_p<float, false>(N, d, g, s);
-  return affine ? launch_volume_ragged_p<double, true>(N, d, g, s) : launch_volume_ragged_p<double, false>(N, d, g, s);
-}
-
-cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
-                                 cudaStream_t s) {
-  const int grid = 8 * sm_count();
-  const bool f32 = precision == NUMA_FP32_MIXED;
-  auto go = [&](auto mode_tag) {
-    constexpr int M = decltype(mode_tag)::value;
-    if (shell) {
-      if (f32) update_ragged<M, true, float><<<grid, 256, 0, s>>>(d, g, stage);
-      else update_ragged<M, true, double><<<grid, 256, 0, s>>>(d, g, stage);
-    } else {
-      if (f32) update_ragged<M, false, float><<<grid, 256, 0, s>>>(d, g, stage);
-      else update_ragged<M, false, double><<<grid, 256, 0, s>>>(d, g, stage);
-    }
-  };
-  // stage 0 of SSP-RK3 is the first stage (a = 0, b = 1)
-  if (stage == 0) go(std::integral_constant<int, 2>());
-  else go(std::integral_constant<int, 1>());
-  return cudaGetLastError();
-}
-
 }  // namespace numa

@@ -42,7 +42,11 @@ PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim) {
   a.Ng = c->mesh.Ng;
   a.precision = c->cfg.precision;
   a.gamma = c->gamma;
-  for (int k = 0; k < kEosTerms; ++k) a.eos[k] = c->eos[k];
+  a.gammaf = (float)c->gamma;
+  for (int k = 0; k < kEosTerms; ++k) {
+    a.eos[k] = c->eos[k];
+    a.eosf[k] = (float)c->eos[k];
+  }
   return a;
 }
 

@@ -85,6 +85,8 @@ struct PrimArgs {
   int precision;
   double gamma;
   double eos[kEosTerms];  // binomial coefficients C(gamma, k), k = 1..kEosTerms
+  float gammaf;           // the same in FP32 for the FP32 form (rounded once, on the host)
+  float eosf[kEosTerms];
 };
 
 // Every element of the mesh maps affinely onto the reference cube (a box
@@ -136,6 +138,11 @@ cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s);
 // until s has run the copy) into the constant table of the FP32 line kernel.
 cudaError_t upload_d32_constant(int N, const float* D, cudaStream_t s);
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s);
+// the element kernels of one precision (volume_fp64.cu, volume_fp32.cu,
+// volume_pairs.cu); launch_volume and launch_volume_ragged dispatch to them
+cudaError_t launch_volume_fp64(int N, bool affine, const VolumeArgs& a, cudaStream_t s);
+cudaError_t launch_volume_fp32(int N, bool affine, const VolumeArgs& a, cudaStream_t s);
+cudaError_t launch_volume_pairs(int N, bool affine, const VolumeArgs& a, cudaStream_t s);
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 
 // ---- serving: ragged multi-member launches --------------------------------
@@ -161,6 +168,9 @@ struct RaggedGroup {
 
 cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
                                  cudaStream_t s);
+cudaError_t launch_volume_ragged_fp64(int N, bool affine, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s);
+cudaError_t launch_volume_ragged_fp32(int N, bool affine, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s);
+cudaError_t launch_volume_ragged_pairs(int N, bool affine, const MemberDesc* d, const RaggedGroup* g, cudaStream_t s);
 cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
                                  cudaStream_t s);
 

@@ -1,0 +1,89 @@
+// Per-global-node kernels of the GB300 NUMA hot path (sm_103a):
+//   prim_kernel   : the primitive fields (u, theta, p') of a state, which the
+//                   element kernels build their fluxes from;
+//   update_kernel : deterministic direct stiffness summation over a
+//                   precomputed inverse map (fixed order, no atomics), inverse
+//                   mass matrix, sources, wall condition, the SSP-RK3 stage
+//                   combination and the primitive fields of the new state;
+// and the launch entry points of all kernels (the element kernels are
+// compiled per precision in volume_fp64.cu, volume_fp32.cu, volume_pairs.cu).
+#include "kernels_common.cuh"
+
+namespace numa {
+
+namespace {
+
+__global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
+  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= a.Ng) return;
+  const long long Ng = a.Ng;
+  write_prim(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
+}
+
+template <int MODE, typename RT>
+void launch_update_m(const UpdateArgs& a, unsigned nb, int nt, cudaStream_t s) {
+  if (a.gvec) update_kernel<MODE, true, RT><<<nb, nt, 0, s>>>(a);
+  else update_kernel<MODE, false, RT><<<nb, nt, 0, s>>>(a);
+}
+
+}  // namespace
+
+cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
+  if (a.Ng == 0) return cudaSuccess;
+  const int nt = 256;
+  prim_kernel<<<(unsigned)((a.Ng + nt - 1) / nt), nt, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_pairs(N, false, a, s);
+  if (precision == NUMA_FP32_MIXED) return launch_volume_fp32(N, a.affine != 0, a, s);
+  return launch_volume_fp64(N, a.affine != 0, a, s);
+}
+
+cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
+  if (a.Ng == 0) return cudaSuccess;
+  const int nt = 256;
+  const unsigned nb = (unsigned)((a.Ng + nt - 1) / nt);
+  const bool f32 = precision == NUMA_FP32_MIXED;
+  if (a.mode == 0) {
+    if (f32) launch_update_m<0, float>(a, nb, nt, s);
+    else launch_update_m<0, double>(a, nb, nt, s);
+  } else if (a.first_stage) {
+    if (f32) launch_update_m<2, float>(a, nb, nt, s);
+    else launch_update_m<2, double>(a, nb, nt, s);
+  } else {
+    if (f32) launch_update_m<1, float>(a, nb, nt, s);
+    else launch_update_m<1, double>(a, nb, nt, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s) {
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_pairs(N, false, d, g, s);
+  if (precision == NUMA_FP32_MIXED) return launch_volume_ragged_fp32(N, affine, d, g, s);
+  return launch_volume_ragged_fp64(N, affine, d, g, s);
+}
+
+cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
+                                 cudaStream_t s) {
+  const int grid = 8 * sm_count();
+  const bool f32 = precision == NUMA_FP32_MIXED;
+  auto go = [&](auto mode_tag) {
+    constexpr int M = decltype(mode_tag)::value;
+    if (shell) {
+      if (f32) update_ragged<M, true, float><<<grid, 256, 0, s>>>(d, g, stage);
+      else update_ragged<M, true, double><<<grid, 256, 0, s>>>(d, g, stage);
+    } else {
+      if (f32) update_ragged<M, false, float><<<grid, 256, 0, s>>>(d, g, stage);
+      else update_ragged<M, false, double><<<grid, 256, 0, s>>>(d, g, stage);
+    }
+  };
+  // stage 0 of SSP-RK3 is the first stage (a = 0, b = 1)
+  if (stage == 0) go(std::integral_constant<int, 2>());
+  else go(std::integral_constant<int, 1>());
+  return cudaGetLastError();
+}
+
+}  // namespace numa
