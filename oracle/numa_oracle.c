@@ -727,3 +727,201 @@ int orc_run(const orc_mesh* m, double* q, double dt, int nsteps) {
   free(work);
   return 0;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Filter (Sec. 2.3 and the time loop of Sec. 6)                            */
+/* ---------------------------------------------------------------------- */
+
+/* Boyd-Vandeven filter weights of the Legendre modes k = 0..N: Vandeven's
+ * filter of order p in Boyd's erfc-log form (J. P. Boyd, 1996).  Modes below
+ * s are kept; for s <= k <= N, with theta = (k - s) / (N - s) and
+ * Omega = theta - 1/2,
+ *   sigma_k = 1/2 erfc(2 sqrt(p) chi Omega),
+ *   chi = sqrt(-log(1 - 4 Omega^2) / (4 Omega^2))   (chi -> 1 as Omega -> 0),
+ * which runs from 1 at theta = 0 to 0 at theta = 1.  A strength mu blends the
+ * filtered and unfiltered values: the applied weight is 1 - mu (1 - sigma_k).
+ * s = N damps only the top mode (theta = 1 there). */
+void orc_filter_weights(int N, int s, double p, double mu, double* sigma) {
+  for (int k = 0; k <= N; ++k) {
+    double sg = 1.0;
+    if (k >= s) {
+      double theta = (s >= N) ? 1.0 : (double)(k - s) / (double)(N - s);
+      double om = theta - 0.5;
+      if (theta <= 0.0) {
+        sg = 1.0;
+      } else if (theta >= 1.0) {
+        sg = 0.0;
+      } else if (om == 0.0) {
+        sg = 0.5;
+      } else {
+        double chi = sqrt(-log(1.0 - 4.0 * om * om) / (4.0 * om * om));
+        sg = 0.5 * erfc(2.0 * sqrt(p) * chi * om);
+      }
+    }
+    sigma[k] = 1.0 - mu * (1.0 - sg);
+  }
+}
+
+/* Invert the n x n matrix A (row-major) by Gauss-Jordan elimination with
+ * partial pivoting.  Returns 0, or -1 if A is singular. */
+static int invert(int n, const double* A, double* Ainv) {
+  double* W = malloc(sizeof(double) * n * 2 * n);
+  if (!W) return -1;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) W[i * 2 * n + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(W[r * 2 * n + c]) > fabs(W[piv * 2 * n + c])) piv = r;
+    if (W[piv * 2 * n + c] == 0.0) {
+      free(W);
+      return -1;
+    }
+    if (piv != c)
+      for (int j = 0; j < 2 * n; ++j) {
+        double t = W[c * 2 * n + j];
+        W[c * 2 * n + j] = W[piv * 2 * n + j];
+        W[piv * 2 * n + j] = t;
+      }
+    double d = W[c * 2 * n + c];
+    for (int j = 0; j < 2 * n; ++j) W[c * 2 * n + j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = W[r * 2 * n + c];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * n; ++j) W[r * 2 * n + j] -= f * W[c * 2 * n + j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ainv[i * n + j] = W[i * 2 * n + n + j];
+  free(W);
+  return 0;
+}
+
+/* The 1D filter matrix F = V diag(sigma) V^-1 on the N+1 Lobatto points, with
+ * the Legendre Vandermonde matrix V_ik = P_k(xi_i): nodal values to modal
+ * coefficients, weights on the modes, back to nodal values.  Row-major
+ * F[i * (N+1) + m].  Returns 0, or -1 on failure. */
+int orc_filter_matrix(int N, int s, double p, double mu, double* F) {
+  int P = N + 1;
+  double xi[ORC_MAXP], w[ORC_MAXP], sigma[ORC_MAXP];
+  double V[ORC_MAXP * ORC_MAXP], Vi[ORC_MAXP * ORC_MAXP];
+  if (N < 1 || N >= ORC_MAXP) return -1;
+  orc_lgl(N, xi, w);
+  for (int i = 0; i < P; ++i) {
+    /* P_0 .. P_N at xi_i by the three-term recurrence */
+    double pkm1 = 1.0, pk = xi[i];
+    V[i * P + 0] = 1.0;
+    if (N >= 1) V[i * P + 1] = xi[i];
+    for (int k = 1; k < N; ++k) {
+      double pkp1 = ((2.0 * k + 1.0) * xi[i] * pk - k * pkm1) / (k + 1.0);
+      pkm1 = pk;
+      pk = pkp1;
+      V[i * P + k + 1] = pk;
+    }
+  }
+  if (invert(P, V, Vi) != 0) return -1;
+  orc_filter_weights(N, s, p, mu, sigma);
+  for (int i = 0; i < P; ++i)
+    for (int m = 0; m < P; ++m) {
+      double acc = 0.0;
+      for (int k = 0; k < P; ++k) acc += V[i * P + k] * sigma[k] * Vi[k * P + m];
+      F[i * P + m] = acc;
+    }
+  return 0;
+}
+
+/* One application of the filter to the global state q (in place), as the
+ * time loop of Sec. 6 states it: per element, the tensor product F x F x F
+ * on the element-node values of each variable; then DSS of the Jw-weighted
+ * element values in ascending element-node order and division by M.  At wall
+ * nodes the wall-normal momentum component keeps its value from before the
+ * filter (the filter does not move mass through a wall).  Returns 0, or -1
+ * / -2 on a bad filter or allocation failure. */
+int orc_filter(const orc_mesh* m, double* q, int s, double p, double mu) {
+  int N = m->N, P = N + 1;
+  long NP = (long)P * P * P, Nl = m->Nl, Ng = m->Ng;
+  double F[ORC_MAXP * ORC_MAXP];
+  if (orc_filter_matrix(N, s, p, mu, F) != 0) return -1;
+  double* acc = calloc((size_t)5 * Ng, sizeof(double));
+  double* u = malloc(sizeof(double) * 2 * NP);
+  if (!acc || !u) {
+    free(acc);
+    free(u);
+    return -2;
+  }
+  double* t = u + NP;
+  for (long e = 0; e < m->Ne; ++e) {
+    for (int v = 0; v < 5; ++v) {
+      for (long l = 0; l < NP; ++l) u[l] = q[v * Ng + m->l2g[e * NP + l]];
+      /* along xi, then eta, then zeta; node l = i + P (j + P k) */
+      for (int k = 0; k < P; ++k)
+        for (int j = 0; j < P; ++j)
+          for (int i = 0; i < P; ++i) {
+            double a = 0.0;
+            for (int mm = 0; mm < P; ++mm) a += F[i * P + mm] * u[mm + P * (j + P * k)];
+            t[i + P * (j + P * k)] = a;
+          }
+      for (int k = 0; k < P; ++k)
+        for (int j = 0; j < P; ++j)
+          for (int i = 0; i < P; ++i) {
+            double a = 0.0;
+            for (int mm = 0; mm < P; ++mm) a += F[j * P + mm] * t[i + P * (mm + P * k)];
+            u[i + P * (j + P * k)] = a;
+          }
+      for (int k = 0; k < P; ++k)
+        for (int j = 0; j < P; ++j)
+          for (int i = 0; i < P; ++i) {
+            double a = 0.0;
+            for (int mm = 0; mm < P; ++mm) a += F[k * P + mm] * u[i + P * (j + P * mm)];
+            t[i + P * (j + P * k)] = a;
+          }
+      for (long l = 0; l < NP; ++l) acc[v * Ng + m->l2g[e * NP + l]] += m->Jw[e * NP + l] * t[l];
+    }
+  }
+  free(u);
+  /* the elements are visited in ascending order, so each global node sums its
+   * element-node contributions in ascending element-node order */
+  for (long g = 0; g < Ng; ++g) {
+    double out[5];
+    for (int v = 0; v < 5; ++v) out[v] = acc[v * Ng + g] / m->M[g];
+    unsigned char b = m->wall[g];
+    if (b & 1) out[1] = q[1 * Ng + g];
+    if (b & 2) out[2] = q[2 * Ng + g];
+    if (b & 4) out[3] = q[3 * Ng + g];
+    if (b & 8) {
+      double x = m->gx[g], y = m->gy[g], z = m->gz[g];
+      double r = sqrt(x * x + y * y + z * z);
+      double n3[3] = {x / r, y / r, z / r};
+      double dn = 0.0, dq = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        dn += out[1 + a] * n3[a];
+        dq += q[(1 + a) * Ng + g] * n3[a];
+      }
+      for (int a = 0; a < 3; ++a) out[1 + a] += (dq - dn) * n3[a];
+    }
+    for (int v = 0; v < 5; ++v) q[v * Ng + g] = out[v];
+  }
+  free(acc);
+  return 0;
+}
+
+/* nsteps SSP-RK3 steps with the filter applied after every `every`-th step
+ * (counted from the first step of this call), in place on q. */
+int orc_run_filtered(const orc_mesh* m, double* q, double dt, int nsteps, int every, int s, double p, double mu) {
+  long n = 5 * m->Ng;
+  double* work = malloc(sizeof(double) * 3 * n);
+  if (!work) return -2;
+  for (int st = 1; st <= nsteps; ++st) {
+    orc_ssprk3_step(n, q, dt, numa_rhs_cb, (void*)m, work);
+    if (every > 0 && st % every == 0) {
+      int rc = orc_filter(m, q, s, p, mu);
+      if (rc != 0) {
+        free(work);
+        return rc;
+      }
+    }
+  }
+  free(work);
+  return 0;
+}

@@ -96,6 +96,16 @@ void orc_ssprk3_step(long n, double* q, double dt, orc_rhs_fn f, void* ctx, doub
 /* nsteps SSP-RK3 steps of the NUMA system, in place on q. */
 int orc_run(const orc_mesh* m, double* q, double dt, int nsteps);
 
+/* Boyd-Vandeven filter (Sec. 2.3): weights sigma[0..N] of the Legendre modes
+ * (first damped mode s, order p, strength mu), the 1D filter matrix
+ * F = V diag(sigma) V^-1 (row-major, (N+1)^2), one application of the filter
+ * to a global state (element-wise F x F x F, Jw-weighted DSS, division by M),
+ * and an SSP-RK3 run with the filter after every `every`-th step. */
+void orc_filter_weights(int N, int s, double p, double mu, double* sigma);
+int orc_filter_matrix(int N, int s, double p, double mu, double* F);
+int orc_filter(const orc_mesh* m, double* q, int s, double p, double mu);
+int orc_run_filtered(const orc_mesh* m, double* q, double dt, int nsteps, int every, int s, double p, double mu);
+
 #ifdef __cplusplus
 }
 #endif

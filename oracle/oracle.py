@@ -82,6 +82,14 @@ def lib():
         L.orc_ssprk3_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
         L.orc_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
         L.orc_run.restype = ctypes.c_int
+        L.orc_filter_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_filter_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_filter_matrix.restype = ctypes.c_int
+        L.orc_filter.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_filter.restype = ctypes.c_int
+        L.orc_run_filtered.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_run_filtered.restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -125,6 +133,21 @@ def dmatrix(N: int) -> np.ndarray:
     D = np.zeros((N + 1) * (N + 1))
     lib().orc_dmatrix(N, _dp(xi), _dp(D))
     return D.reshape(N + 1, N + 1)
+
+
+def filter_weights(N: int, s: int, p: float, mu: float = 1.0) -> np.ndarray:
+    """Boyd-Vandeven weights of the Legendre modes 0..N (Sec. 2.3)."""
+    sigma = np.zeros(N + 1)
+    lib().orc_filter_weights(N, s, p, mu, _dp(sigma))
+    return sigma
+
+
+def filter_matrix(N: int, s: int, p: float, mu: float = 1.0) -> np.ndarray:
+    """1D filter matrix F = V diag(sigma) V^-1 on the Lobatto points."""
+    F = np.zeros((N + 1) * (N + 1))
+    if lib().orc_filter_matrix(N, s, p, mu, _dp(F)) != 0:
+        raise ValueError("bad filter")
+    return F.reshape(N + 1, N + 1)
 
 
 def pprime(Th_pert: float, Th0: float, p0: float, gamma: float) -> float:
@@ -235,4 +258,18 @@ class Mesh:
         rc = lib().orc_run(self._h, _dp(q), dt, nsteps)
         if rc != 0:
             raise MemoryError("oracle run failed")
+        return q
+
+    def filter(self, q: np.ndarray, s: int, p: float, mu: float = 1.0) -> np.ndarray:
+        """One application of the Boyd-Vandeven filter with DSS (Sec. 6 loop)."""
+        q = np.ascontiguousarray(q, dtype=np.float64).copy()
+        if lib().orc_filter(self._h, _dp(q), s, p, mu) != 0:
+            raise ValueError("oracle filter failed")
+        return q
+
+    def run_filtered(self, q: np.ndarray, dt: float, nsteps: int, every: int, s: int, p: float,
+                     mu: float = 1.0) -> np.ndarray:
+        q = np.ascontiguousarray(q, dtype=np.float64).copy()
+        if lib().orc_run_filtered(self._h, _dp(q), dt, nsteps, every, s, p, mu) != 0:
+            raise ValueError("oracle filtered run failed")
         return q
