@@ -172,6 +172,30 @@ int numa_rk_step(numa_ctx* ctx, double dt);
  * non-finite value. */
 int numa_run(numa_ctx* ctx, double dt, int nsteps);
 
+/* Boyd-Vandeven filter (Sec. 2.3), applied as in the time loop of Sec. 6:
+ * after every `every`-th step of numa_run / numa_rk_step (the count restarts
+ * at numa_set_filter, numa_set_state and numa_init_state), the state becomes
+ *   q <- M^-1 DSS(Jw (F x F x F) q_e),
+ * the tensor product over each element of the 1D modal filter
+ * F = V diag(sigma) V^-1 (V_ik = P_k(xi_i), Legendre modes k = 0..N on the
+ * Lobatto points), followed by direct stiffness summation of the
+ * Jw-weighted element values and the inverse mass matrix.  sigma_k = 1 for
+ * k < s; for s <= k <= N Vandeven's filter of order p in Boyd's erfc-log
+ * form, 1/2 erfc(2 sqrt(p) chi O), O = theta - 1/2,
+ * theta = (k - s)/(N - s), chi^2 = -log(1 - 4 O^2)/(4 O^2): 1 at k = s, 0 at
+ * k = N; blended with the identity by the strength mu: 1 - mu (1 - sigma_k).
+ * At wall nodes the wall-normal momentum keeps its value.  The filter
+ * computes in FP64 (FP32 for the element part in the FP32-mixed form; the
+ * state update stays FP64).
+ * every >= 0 (0: never applied by run / rk_step), 0 <= s <= N+1 (N+1: no
+ * mode damped), p > 0, 0 <= mu <= 1; otherwise NUMA_EINVAL.  May be called
+ * before numa_bind; a bound context uploads the matrix and waits. */
+int numa_set_filter(numa_ctx* ctx, int every, int s, double p, double mu);
+
+/* Apply the filter once to the context's state, now (enqueued on the bound
+ * stream).  NUMA_ESTATE before numa_set_filter or numa_bind. */
+int numa_filter(numa_ctx* ctx);
+
 /* Measurement helper: advance the state by nsteps SSP-RK3 steps with plain
  * (non-graph) launches, bracketing every kernel with CUDA events on the
  * bound stream, then wait and return the summed device time in ms of the

@@ -19,8 +19,8 @@ LIB = os.path.join(HERE, "libnuma_gb300.so")
 
 # the element kernels of each precision are separate units so that they
 # compile in parallel
-SOURCES = ["mesh.cpp", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu", "numa_api.cu",
-           "noalloc.cu", "serve.cu"]
+SOURCES = ["mesh.cpp", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu", "filter.cu",
+           "numa_api.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code (the mesh and geometry setup) is compiled without floating-point
 # contraction so that node coordinates come out bitwise the same on x86-64

@@ -758,7 +758,9 @@ __device__ __forceinline__ double re_load(const void* re, long long idx) {
 // DSS, inverse mass, sources, walls and the stage update at global node I of
 // one mesh (shared by the single-mesh and the ragged kernels).  MODE 0 writes
 // the tendency R; MODE 1 a general RK stage; MODE 2 the first stage (a = 0,
-// b = 1: no q^n read, no q^n term).
+// b = 1: no q^n read, no q^n term); MODE 3 the DSS of the filter correction,
+// q + M^-1 DSS(Jw ((F x F x F) q - q)), with the wall-normal momentum left as
+// it was.
 template <int MODE, bool SHELL, typename RT>
 __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
   const long long Ng = a.Ng, Nl = a.Nl;
@@ -779,6 +781,32 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
   const double minv = a.Minv[I];
   const double rp = a.qk[I];
   const uint8_t w = a.wall[I];
+  if constexpr (MODE == 3) {
+    double c1 = s1 * minv, c2 = s2 * minv, c3 = s3 * minv;
+    if constexpr (SHELL) {
+      if (w & 8) {  // no radial correction at the bottom and lid
+        const double nx = a.nrm[I], ny = a.nrm[Ng + I], nz = a.nrm[2 * Ng + I];
+        const double dot = c1 * nx + c2 * ny + c3 * nz;
+        c1 -= dot * nx;
+        c2 -= dot * ny;
+        c3 -= dot * nz;
+      }
+    } else {
+      if (w & 1) c1 = 0.0;
+      if (w & 2) c2 = 0.0;
+      if (w & 4) c3 = 0.0;
+    }
+    const double y0 = fma(s0, minv, rp), y1 = a.qk[Ng + I] + c1, y2 = a.qk[2 * Ng + I] + c2;
+    const double y3 = a.qk[3 * Ng + I] + c3, y4 = fma(s4, minv, a.qk[4 * Ng + I]);
+    a.out[I] = y0;
+    a.out[Ng + I] = y1;
+    a.out[2 * Ng + I] = y2;
+    a.out[3 * Ng + I] = y3;
+    a.out[4 * Ng + I] = y4;
+    if (nonfinite(y0) | nonfinite(y1) | nonfinite(y2) | nonfinite(y3) | nonfinite(y4)) atomicOr(a.flag, 1);
+    write_prim(a.pa, I, y0, y1, y2, y3, y4);
+    return;
+  }
   if constexpr (MODE == 0 || SHELL) {
     // R = M^-1 DSS(r_e) + S, then the wall condition
     double R0 = s0 * minv, R1 = s1 * minv, R2 = s2 * minv, R3 = s3 * minv, R4 = s4 * minv;

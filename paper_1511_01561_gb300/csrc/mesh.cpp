@@ -214,6 +214,51 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
 
 }  // namespace
 
+// Boyd-Vandeven filter (Sec. 2.3).  Weight of Legendre mode k: 1 below the
+// first damped mode s; above it Vandeven's filter of order p in Boyd's
+// erfc-log form, 1/2 erfc(2 sqrt(p) chi(O) O) with O = theta - 1/2,
+// theta = (k - s)/(N - s) and chi(O)^2 = -log(1 - 4 O^2) / (4 O^2), which is 1
+// at theta = 0 and 0 at theta = 1; blended with the identity by mu.
+// The matrix F = V diag(sigma) V^-1 uses V_ik = P_k(xi_i) and its inverse from
+// the discrete orthogonality of the Legendre polynomials under Lobatto
+// quadrature: sum_i w_i P_j(xi_i) P_k(xi_i) = delta_jk g_k with g_k = 2/(2k+1)
+// for k < N and g_N = 2/N (the quadrature is exact up to degree 2N-1), so
+// (V^-1)_ki = w_i P_k(xi_i) / g_k.
+void filter_matrix_host(int N, const double* xi, const double* w, int s, double p, double mu, double* F) {
+  const int P = N + 1;
+  std::vector<double> sigma(P), V(P * P);
+  for (int k = 0; k < P; ++k) {
+    double sg = 1.0;
+    if (k >= s) {
+      const double theta = s >= N ? 1.0 : double(k - s) / double(N - s);
+      const double o = theta - 0.5;
+      if (theta >= 1.0) sg = 0.0;
+      else if (theta > 0.0) sg = o == 0.0 ? 0.5 : 0.5 * std::erfc(2.0 * std::sqrt(p) * std::sqrt(-std::log(1.0 - 4.0 * o * o) / (4.0 * o * o)) * o);
+    }
+    sigma[k] = 1.0 - mu * (1.0 - sg);
+  }
+  for (int i = 0; i < P; ++i) {
+    double a = 1.0, b = xi[i];
+    V[i * P] = 1.0;
+    if (P > 1) V[i * P + 1] = b;
+    for (int k = 2; k < P; ++k) {
+      const double c = ((2 * k - 1) * xi[i] * b - (k - 1) * a) / k;
+      a = b;
+      b = c;
+      V[i * P + k] = c;
+    }
+  }
+  for (int i = 0; i < P; ++i)
+    for (int m = 0; m < P; ++m) {
+      double acc = 0.0;
+      for (int k = 0; k < P; ++k) {
+        const double gk = k < N ? 2.0 / (2.0 * k + 1.0) : 2.0 / N;
+        acc += V[i * P + k] * sigma[k] * (w[m] * V[m * P + k] / gk);
+      }
+      F[i * P + m] = acc;
+    }
+}
+
 bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
   if (c.N < 1 || c.N > kMaxN) {
     err = "N must be in 1..8";

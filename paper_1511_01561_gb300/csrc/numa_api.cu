@@ -98,6 +98,41 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   return a;
 }
 
+FilterArgs filter_args(const numa_ctx* c) {
+  FilterArgs a;
+  a.q = c->L.q;
+  a.l2g = c->L.l2g;
+  a.F = c->cfg.precision == NUMA_FP32_MIXED ? (const void*)c->L.F32 : (const void*)c->L.F64;
+  a.met64 = c->L.met64;
+  a.met32 = c->L.met32;
+  a.met2 = c->L.met2;
+  a.re = c->L.re;
+  a.Ng = c->mesh.Ng;
+  a.Nl = c->mesh.Nl;
+  a.Ne = (int)c->mesh.Ne;
+  return a;
+}
+
+// The filter matrix (FP64 and FP32 copies) into the bound workspace.
+cudaError_t upload_filter(numa_ctx* c) {
+  const size_t PP = c->filter_F.size();
+  std::vector<float> f32(PP);
+  for (size_t t = 0; t < PP; ++t) f32[t] = (float)c->filter_F[t];
+  cudaError_t e = cudaMemcpyAsync(c->L.F64, c->filter_F.data(), PP * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->L.F32, f32.data(), PP * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
+// One application of the filter to the state, in place on stream s; leaves
+// the primitive fields of the filtered state.
+cudaError_t enqueue_filter(numa_ctx* c, cudaStream_t s) {
+  cudaError_t e = launch_filter(c->mesh.N, c->cfg.precision, filter_args(c), s);
+  if (e == cudaSuccess)
+    e = launch_update(c->cfg.precision, update_args(c, c->L.re, c->L.q, c->L.q, c->L.q, 3, 0.0, 1.0, 1.0), s);
+  return e;
+}
+
 // R(q) into r_dev with the given primitive and residual scratch.
 cudaError_t enqueue_rhs(numa_ctx* c, const double* q, double* r, void* prim, void* re) {
   cudaError_t e = launch_prim(prim_args(c, q, prim), c->stream);
@@ -176,6 +211,8 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.D64 = (double*)take(PP * 8);
   d.D32 = (float*)take(PP * 4);
   d.D2 = (float2*)take(PP * 8);
+  d.F64 = (double*)take(PP * 8);
+  d.F32 = (float*)take(PP * 4);
   d.bytes = off;
   if (L) *L = d;
   return off;
@@ -315,6 +352,14 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  if (c->fgraph) {
+    cudaGraphExecDestroy(c->fgraph);
+    c->fgraph = nullptr;
+  }
+  if (c->filter_set) {
+    e = upload_filter(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind filter upload");
+  }
   return NUMA_OK;
 }
 
@@ -330,6 +375,7 @@ int numa_init_state(numa_ctx* c, int kind, const double* params, int nparams) {
   }
   if (!init_state_host(c->cfg, c->mesh, kind, params, nparams, q.data(), c->err)) return NUMA_EINVAL;
   c->prim_valid = false;
+  c->filter_count = 0;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q.data(), q.size() * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_init_state upload");
@@ -340,6 +386,7 @@ int numa_set_state(numa_ctx* c, const double* q, int on_device) {
   if (!c || !q) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_set_state before numa_bind");
   c->prim_valid = false;
+  c->filter_count = 0;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
@@ -373,6 +420,10 @@ int numa_rk_step(numa_ctx* c, double dt) {
   if (!std::isfinite(dt)) return fail(c, NUMA_EINVAL, "dt must be finite");
   cudaError_t e = ensure_prim(c);
   if (e == cudaSuccess) e = enqueue_rk_step(c, dt, c->stream);
+  if (e == cudaSuccess && c->filter_every > 0 && ++c->filter_count == c->filter_every) {
+    e = enqueue_filter(c, c->stream);
+    c->filter_count = 0;
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_rk_step launch");
   return NUMA_OK;
 }
@@ -401,8 +452,31 @@ int numa_run(numa_ctx* c, double dt, int nsteps) {
     c->graph_dt = dt;
     c->graph_q = c->L.q;
   }
+  if (c->filter_every > 0 && (!c->fgraph || c->fgraph_q != c->L.q)) {
+    if (c->fgraph) {
+      cudaGraphExecDestroy(c->fgraph);
+      c->fgraph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = enqueue_filter(c, c->cap_stream);
+      e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->fgraph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_run filter graph capture");
+    c->fgraph_q = c->L.q;
+  }
   if (nsteps > 0) e = ensure_prim(c);
-  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = cudaGraphLaunch(c->graph, c->stream);
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
+    e = cudaGraphLaunch(c->graph, c->stream);
+    if (e == cudaSuccess && c->filter_every > 0 && ++c->filter_count == c->filter_every) {
+      e = cudaGraphLaunch(c->fgraph, c->stream);
+      c->filter_count = 0;
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_run graph launch");
   int flag = 0;
   int rc = numa_check_finite(c, &flag);
@@ -461,9 +535,43 @@ const char* numa_last_error(const numa_ctx* c) {
   return c->err.c_str();
 }
 
+int numa_set_filter(numa_ctx* c, int every, int s, double p, double mu) {
+  if (!c) return NUMA_EINVAL;
+  const int N = c->mesh.N;
+  if (every < 0) return fail(c, NUMA_EINVAL, "filter: every must be >= 0");
+  if (s < 0 || s > N + 1) return fail(c, NUMA_EINVAL, "filter: s must be in [0, N+1]");
+  if (!(p > 0.0) || !std::isfinite(p)) return fail(c, NUMA_EINVAL, "filter: order p must be positive");
+  if (!(mu >= 0.0 && mu <= 1.0)) return fail(c, NUMA_EINVAL, "filter: strength mu must be in [0, 1]");
+  std::vector<double> F((size_t)(N + 1) * (N + 1));
+  filter_matrix_host(N, c->mesh.xi.data(), c->mesh.w.data(), s, p, mu, F.data());
+  c->filter_F = F;
+  c->filter_set = true;
+  c->filter_every = every;
+  c->filter_s = s;
+  c->filter_p = p;
+  c->filter_mu = mu;
+  c->filter_count = 0;
+  if (c->bound) {
+    cudaError_t e = upload_filter(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_set_filter upload");
+  }
+  return NUMA_OK;
+}
+
+int numa_filter(numa_ctx* c) {
+  if (!c) return NUMA_EINVAL;
+  if (!c->bound) return fail(c, NUMA_ESTATE, "numa_filter before numa_bind");
+  if (!c->filter_set) return fail(c, NUMA_ESTATE, "numa_filter before numa_set_filter");
+  cudaError_t e = enqueue_filter(c, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "numa_filter launch");
+  c->prim_valid = true;
+  return NUMA_OK;
+}
+
 int numa_destroy(numa_ctx* c) {
   if (!c) return NUMA_EINVAL;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->fgraph) cudaGraphExecDestroy(c->fgraph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return NUMA_OK;

@@ -68,6 +68,8 @@ struct DevLayout {
   double* nrm = nullptr;     // [3][Ng] (shell)
   double* D64 = nullptr;     // [P*P]
   float* D32 = nullptr;      // [P*P]
+  double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
+  float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
   int* flags = nullptr;      // [64]: 0 = non-finite
   size_t bytes = 0;
 };
@@ -128,9 +130,22 @@ struct UpdateArgs {
   double a, b, dt;     // out = a qn + b (qk + dt R)
   double bdt, bdtg;    // b dt and b dt g, computed once on the host
   int first_stage;     // 1 when a = 0 and b = 1 (no q^n term)
-  int mode;            // 0: write R, 1: RK stage (also writes the primitives of out)
+  int mode;            // 0: write R, 1: RK stage, 3: filter DSS (1 and 3 also write the primitives of out)
   int* flag;           // non-finite flag
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
+};
+
+// One application of the Boyd-Vandeven filter (element part).
+struct FilterArgs {
+  const double* q;       // state [5][Ng]
+  const int32_t* l2g;
+  const void* F;         // 1D filter matrix [(N+1)^2]: double (FP64, pairs) or float (FP32 form)
+  const double* met64;   // Jw is row 9 of whichever metric array the precision stores
+  const float* met32;
+  const float2* met2;
+  void* re;              // [5][Nl] Jw-weighted correction, double or float like the residuals
+  long long Ng, Nl;
+  int Ne;
 };
 
 cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s);
@@ -144,6 +159,8 @@ cudaError_t launch_volume_fp64(int N, bool affine, const VolumeArgs& a, cudaStre
 cudaError_t launch_volume_fp32(int N, bool affine, const VolumeArgs& a, cudaStream_t s);
 cudaError_t launch_volume_pairs(int N, bool affine, const VolumeArgs& a, cudaStream_t s);
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
+// the element part of the filter (filter.cu); mode 3 of launch_update does the DSS
+cudaError_t launch_filter(int N, int precision, const FilterArgs& a, cudaStream_t s);
 
 // ---- serving: ragged multi-member launches --------------------------------
 
@@ -192,6 +209,14 @@ struct numa_ctx {
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   const double* graph_q = nullptr;
+  // Boyd-Vandeven filter: parameters (set by numa_set_filter), its host
+  // matrix, and the steps since it was last applied
+  bool filter_set = false;
+  int filter_every = 0, filter_s = 0, filter_count = 0;
+  double filter_p = 0.0, filter_mu = 0.0;
+  std::vector<double> filter_F;
+  cudaGraphExec_t fgraph = nullptr;
+  const double* fgraph_q = nullptr;
 };
 
 namespace numa {
@@ -204,6 +229,10 @@ PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim);
 VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, void* re);
 UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, const double* qn, double* out,
                        int mode, double ra, double rb, double dt);
+FilterArgs filter_args(const numa_ctx* c);
+// Boyd-Vandeven weights and the 1D filter matrix F = V diag(sigma) V^-1 of
+// order N on the Lobatto points xi with weights w (mesh.cpp).
+void filter_matrix_host(int N, const double* xi, const double* w, int s, double p, double mu, double* F);
 cudaError_t ensure_prim(numa_ctx* c);
 
 }  // namespace numa

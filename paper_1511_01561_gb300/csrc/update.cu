@@ -49,6 +49,9 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   if (a.mode == 0) {
     if (f32) launch_update_m<0, float>(a, nb, nt, s);
     else launch_update_m<0, double>(a, nb, nt, s);
+  } else if (a.mode == 3) {
+    if (f32) launch_update_m<3, float>(a, nb, nt, s);
+    else launch_update_m<3, double>(a, nb, nt, s);
   } else if (a.first_stage) {
     if (f32) launch_update_m<2, float>(a, nb, nt, s);
     else launch_update_m<2, double>(a, nb, nt, s);

@@ -67,6 +67,8 @@ def _load():
         "numa_rhs_static_scratch": [vp, vp, vp],
         "numa_rk_step": [vp, d],
         "numa_run": [vp, d, i],
+        "numa_set_filter": [vp, i, i, d, d],
+        "numa_filter": [vp],
         "numa_check_finite": [vp, ctypes.POINTER(i)],
         "numa_time_kernels": [vp, d, i, dp, dp],
         "numa_get_coords": [vp, dp],
@@ -176,6 +178,14 @@ def numa_run(ctx, dt: float, nsteps: int) -> None:
     _check(ctx, lib.numa_run(ctx, dt, nsteps))
 
 
+def numa_set_filter(ctx, every: int, s: int, p: float, mu: float = 1.0) -> None:
+    _check(ctx, lib.numa_set_filter(ctx, int(every), int(s), float(p), float(mu)))
+
+
+def numa_filter(ctx) -> None:
+    _check(ctx, lib.numa_filter(ctx))
+
+
 def numa_time_kernels(ctx, dt: float, nsteps: int):
     """(ms of volume kernels, ms of DSS/update kernels) over nsteps RK3 steps."""
     a, b = ctypes.c_double(), ctypes.c_double()
@@ -276,6 +286,14 @@ class Solver:
 
     def run(self, dt: float, nsteps: int):
         numa_run(self.ctx, dt, nsteps)
+
+    def set_filter(self, every: int, s: int, p: float, mu: float = 1.0):
+        """Boyd-Vandeven filter after every `every`-th step (0: off)."""
+        numa_set_filter(self.ctx, every, s, p, mu)
+
+    def filter(self):
+        """Apply the filter once to the state now."""
+        numa_filter(self.ctx)
 
     def time_kernels(self, dt: float, nsteps: int):
         return numa_time_kernels(self.ctx, dt, nsteps)

@@ -98,6 +98,15 @@ def test_argument_errors_without_gpu(numa):
             numa.numa_bind(ctx, 256, 16, 0)
         assert e.value.code == -2  # workspace too small
         assert "workspace" in numa.numa_last_error(ctx)
+        # the filter can be configured before binding; bad parameters are refused
+        numa.numa_set_filter(ctx, 1, 2, 12.0, 0.5)
+        for bad in ((-1, 2, 12.0, 1.0), (1, 4, 12.0, 1.0), (1, 2, -3.0, 1.0), (1, 2, 12.0, -0.1)):
+            with pytest.raises(numa.NumaError) as e:
+                numa.numa_set_filter(ctx, *bad)
+            assert e.value.code == -1
+        with pytest.raises(numa.NumaError) as e:
+            numa.numa_filter(ctx)
+        assert e.value.code == -7  # not bound
     finally:
         numa.numa_destroy(ctx)
     assert numa.lib.numa_destroy(None) == -1
