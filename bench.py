@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--filter-reps", type=int, default=20, help="filter applications timed (0 skips)")
     p.add_argument("--serve", action="store_true", help="ensemble-serving workload instead of the RK3 steps")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-steps-scale", type=float, default=1.0, help="scale every request's step count")
@@ -97,6 +98,13 @@ def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
     fluxes U_x (B_d.u) + B_dx p', 3 each; theta (B_d.U), 1; then 5 products
     with -Jw)."""
     return 30.0 * (N + 1) + 65.0 if affine else 78.0 * (N + 1) + 150.0
+
+
+def filter_flops_per_elem_node(N: int) -> float:
+    """Algorithmic flops per element node of the filter's element part: three
+    contractions of length N+1 on five variables, the subtraction of q and
+    the Jw weight."""
+    return 30.0 * (N + 1) + 10.0
 
 
 def volume_bytes(Nl: int, Ng: int, fp: int, N: int = 4, affine: bool = False) -> float:
@@ -301,11 +309,24 @@ def run_mine(args):
             te = max_over_ranks(time.perf_counter() - t0)
             e2e = {"value": world * s.Ng * STAGES * args.steps / te, "unit": UNIT,
                    "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        filt = None
+        if (precision, form) == ("fp64", "auto") and args.filter_reps > 0:
+            # Boyd-Vandeven filter (element kernel + DSS update), applied on its own
+            s.set_filter(0, max(0, w["cfg"]["N"] - 1), 12.0, 1.0)
+            s.filter()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            f0.record(stream)
+            for _ in range(args.filter_reps):
+                s.filter()
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            filt = f0.elapsed_time(f1) / args.filter_reps
         finite = s.check_finite() == 0
         s.close()
-        return ms, ms_vol, ms_upd, info, e2e, ck, finite
+        return ms, ms_vol, ms_upd, info, e2e, ck, finite, filt
 
-    ms, ms_vol, ms_upd, info, e2e, ck, finite = measure("fp64")
+    ms, ms_vol, ms_upd, info, e2e, ck, finite, filt_ms = measure("fp64")
     Ng, Nl, N = info["Ng"], info["Nl"], info["N"]
     value = world * Ng * STAGES * args.steps / (ms * 1e-3)
     nlaunch = STAGES * args.steps
@@ -336,10 +357,18 @@ def run_mine(args):
         "clocks": ck,
         "finite": finite,
     }
+    if filt_ms is not None:
+        ff = filter_flops_per_elem_node(N) * Nl
+        line["filter"] = {
+            "what": "one Boyd-Vandeven filter application (element kernel + DSS), FP64, s = N-1, p = 12",
+            "ms_per_application": filt_ms, "reps": args.filter_reps,
+            "element_fp64_tflops_lower_bound": ff / (filt_ms * 1e-3) / 1e12,
+            "frac_of_fp64_peak_lower_bound": ff / (filt_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+        }
     if affine:
         # the same workload through the per-node form of Eq. 5 (metric terms
         # read and applied at every node), for comparison
-        msn, voln, updn, _, _, _, finn = measure("fp64", "nodal")
+        msn, voln, updn, _, _, _, finn, _ = measure("fp64", "nodal")
         voln_s = voln * 1e-3 / nlaunch
         fl_n = volume_flops_per_elem_node(N, False) * Nl
         line["fp64_nodal_form"] = {
@@ -351,7 +380,7 @@ def run_mine(args):
                          "traffic": ncu_traffic("volume_fp64_nodal")},
         }
     if not args.no_fp32:
-        ms32, vol32, upd32, _, _, _, fin32 = measure("fp32_mixed")
+        ms32, vol32, upd32, _, _, _, fin32, _ = measure("fp32_mixed")
         v32 = world * Ng * STAGES * args.steps / (ms32 * 1e-3)
         vol32_s = vol32 * 1e-3 / nlaunch
         b = volume_bytes(Nl, Ng, 4, N, affine)
@@ -367,7 +396,7 @@ def run_mine(args):
             "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
         }
         if affine:
-            ms32n, vol32n, _, _, _, _, fin32n = measure("fp32_mixed", "nodal")
+            ms32n, vol32n, _, _, _, _, fin32n, _ = measure("fp32_mixed", "nodal")
             vol32n_s = vol32n * 1e-3 / nlaunch
             bn = volume_bytes(Nl, Ng, 4)
             line["fp32_mixed"]["nodal_form"] = {
@@ -376,17 +405,22 @@ def run_mine(args):
                 "traffic": ncu_traffic("volume_fp32_nodal")}
     if not args.no_fp32:
         # FP64-accurate element kernel on the FP32 units ((hi, lo) float pairs)
-        msp, volp, updp, _, _, _, finp = measure("fp64_pairs")
+        msp, volp, updp, _, _, _, finp, _ = measure("fp64_pairs")
         vp = world * Ng * STAGES * args.steps / (msp * 1e-3)
         volp_s = volp * 1e-3 / nlaunch
-        bp = volume_bytes(Nl, Ng, 8)
+        bp = volume_bytes(Nl, Ng, 8, N, affine)
         line["fp64_pairs"] = {
             "value": vp, "unit": UNIT, "ms_per_step": msp / args.steps, "speedup_vs_fp64": vp / value,
-            "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
-            "volume_fp64_equiv_tflops": volume_flops_per_elem_node(N, False) * Nl / volp_s / 1e12,
-            "volume_traffic": ncu_traffic("volume_pairs"),
+            "form": form_name, "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
+            "volume_fp64_equiv_tflops": volume_flops_per_elem_node(N, affine) * Nl / volp_s / 1e12,
+            "volume_traffic": ncu_traffic(f"volume_pairs_{form_name}"),
             "volume_hbm_gbs": bp / volp_s / 1e9, "volume_hbm_frac": bp / volp_s / 1e9 / hbm_gbs,
         }
+        if affine:
+            mspn, volpn, _, _, _, _, finpn, _ = measure("fp64_pairs", "nodal")
+            line["fp64_pairs"]["nodal_form"] = {
+                "value": world * Ng * STAGES * args.steps / (mspn * 1e-3), "ms_per_step": mspn / args.steps,
+                "finite": finpn, "volume_ms_avg": volpn / nlaunch}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

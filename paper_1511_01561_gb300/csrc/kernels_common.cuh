@@ -722,6 +722,95 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   re[4 * Nl + n] = -join64(pp_mul(jw, pp_norm(th_, tl)));
 }
 
+// create_rhs of an affine element in the pairs mode: the contravariant
+// fluxes of stage_fluxes_affine in (hi, lo) float pairs, less their values
+// at element node 0, and three contractions with D per equation.  smem_raw
+// holds 15 (N+1)^3 + (N+1)^2 + 15 pairs.
+template <int N>
+__device__ __forceinline__ void volume_element_pairs_affine(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  Pairs* G = reinterpret_cast<Pairs*>(smem_raw);  // [15][NP]
+  Pairs* Ds = G + 15 * NP;                         // [P][P]
+  Pairs* base = Ds + P * P;                        // [15]: the fluxes at element node 0
+  const Pairs* Dg = reinterpret_cast<const Pairs*>(a.D2);
+  const Pairs* met = reinterpret_cast<const Pairs*>(a.met2);
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
+  const long long e0 = e * NP, n = e0 + l;
+  const long long Ng = a.Ng, Nl = a.Nl;
+  if (l < NP) {
+    Pairs B[9];  // the element's metric terms, at its first node
+#pragma unroll
+    for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + e0];
+    const int g = a.l2g[n];
+    const Pairs* w = static_cast<const Pairs*>(a.prim);
+    const Pairs Ux = w[g], Uy = w[Ng + g], Uz = w[2 * Ng + g];
+    const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
+    const Pairs th = w[6 * Ng + g];
+    // p' relative to its value at element node 0: B_dc p'(node 0) is constant
+    // over the element and D annihilates it, and the difference keeps the
+    // pressure term's rounding at the level of its variation, not of p'
+    const Pairs pp = pp_sub(w[7 * Ng + g], w[7 * Ng + a.l2g[e0]]);
+    Pairs v[15];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float h, lo;
+      pp_first(h, lo, B[3 * d], ux);
+      pp_fma(h, lo, B[3 * d + 1], uy);
+      pp_fma(h, lo, B[3 * d + 2], uz);
+      const Pairs ud = pp_norm(h, lo);  // B_d . u
+      pp_first(h, lo, B[3 * d], Ux);
+      pp_fma(h, lo, B[3 * d + 1], Uy);
+      pp_fma(h, lo, B[3 * d + 2], Uz);
+      const Pairs Gr = pp_norm(h, lo);  // B_d . U
+      v[d] = Gr;
+      pp_first(h, lo, Ux, ud);
+      pp_fma(h, lo, B[3 * d], pp);
+      v[3 + d] = pp_norm(h, lo);
+      pp_first(h, lo, Uy, ud);
+      pp_fma(h, lo, B[3 * d + 1], pp);
+      v[6 + d] = pp_norm(h, lo);
+      pp_first(h, lo, Uz, ud);
+      pp_fma(h, lo, B[3 * d + 2], pp);
+      v[9 + d] = pp_norm(h, lo);
+      v[12 + d] = pp_mul(th, Gr);
+    }
+#pragma unroll
+    for (int f = 0; f < 15; ++f) G[f * NP + l] = v[f];
+    if (l == 0) {
+#pragma unroll
+      for (int f = 0; f < 15; ++f) base[f] = v[f];
+    }
+  }
+  __syncthreads();
+  // D annihilates constants: differentiate G - G(node 0), as in the per-node form
+  if (l < NP) {
+#pragma unroll
+    for (int f = 0; f < 15; ++f) G[f * NP + l] = pp_sub(G[f * NP + l], base[f]);
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  const Pairs jw = met[9 * Nl + n];
+  double* re = static_cast<double*>(a.re);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const Pairs* g0 = G + (3 * v) * NP;
+    const Pairs* g1 = g0 + NP;
+    const Pairs* g2 = g1 + NP;
+    float h, lo;
+    pp_first(h, lo, Ds[i * P], g0[bx]);
+#pragma unroll
+    for (int m = 1; m < P; ++m) pp_fma(h, lo, Ds[i * P + m], g0[bx + m]);
+#pragma unroll
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[j * P + m], g1[by + P * m]);
+#pragma unroll
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[k * P + m], g2[bz + P * P * m]);
+    re[v * Nl + n] = -join64(pp_mul(jw, pp_norm(h, lo)));
+  }
+}
+
 // Dynamic shared memory of one element: the staged fluxes, D and (pairs
 // mode) the node-0 base values.
 template <int N, typename T, bool AFF>
@@ -729,15 +818,17 @@ constexpr size_t element_smem_bytes() {
   constexpr int P = N + 1, NP = P * P * P;
   if constexpr (std::is_same<T, float>::value) return sizeof(float) * (kNF > 15 ? kNF : 15) * NP;
   if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (15 * NP + P * P);
+  if constexpr (AFF) return sizeof(T) * (15 * NP + P * P + 15);
   return sizeof(T) * (kNF * NP + P * P + kNF);
 }
 
-// Element kernel of one precision; AFF selects the affine-element form
-// (FP64 and FP32; the pairs mode has only the general form).
+// Element kernel of one precision; AFF selects the affine-element form.
 template <int N, typename T, bool AFF>
 __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
-  if constexpr (std::is_same<T, Pairs>::value) volume_element_pairs<N>(a, e, smem_raw);
-  else if constexpr (std::is_same<T, float>::value) volume_element_lines<N, AFF>(a, e, smem_raw);
+  if constexpr (std::is_same<T, Pairs>::value) {
+    if constexpr (AFF) volume_element_pairs_affine<N>(a, e, smem_raw);
+    else volume_element_pairs<N>(a, e, smem_raw);
+  } else if constexpr (std::is_same<T, float>::value) volume_element_lines<N, AFF>(a, e, smem_raw);
   else if constexpr (AFF) volume_element_affine<N, T>(a, e, smem_raw);
   else volume_element<N, T>(a, e, smem_raw);
 }

@@ -36,7 +36,7 @@ cudaError_t launch_prim(const PrimArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_t s) {
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_pairs(N, false, a, s);
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_pairs(N, a.affine != 0, a, s);
   if (precision == NUMA_FP32_MIXED) return launch_volume_fp32(N, a.affine != 0, a, s);
   return launch_volume_fp64(N, a.affine != 0, a, s);
 }
@@ -64,7 +64,7 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
 
 cudaError_t launch_volume_ragged(int N, int precision, bool affine, const MemberDesc* d, const RaggedGroup* g,
                                  cudaStream_t s) {
-  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_pairs(N, false, d, g, s);
+  if (precision == NUMA_FP64_PAIRS) return launch_volume_ragged_pairs(N, affine, d, g, s);
   if (precision == NUMA_FP32_MIXED) return launch_volume_ragged_fp32(N, affine, d, g, s);
   return launch_volume_ragged_fp64(N, affine, d, g, s);
 }

@@ -99,7 +99,7 @@ def test_rhs_parity_box(numa, orc, name, cfg, kind, precision):
 NODAL_CASES = [c for c in BOX_CASES if c[1].get("warp", 0.0) == 0.0]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_pairs", "fp32_mixed"])
 @pytest.mark.parametrize("name,cfg,kind", NODAL_CASES, ids=[c[0] for c in NODAL_CASES])
 def test_rhs_parity_box_nodal_form(numa, orc, name, cfg, kind, precision):
     m = orc.Mesh(cfg)
@@ -107,7 +107,7 @@ def test_rhs_parity_box_nodal_form(numa, orc, name, cfg, kind, precision):
     Ro = m.rhs(q)
     Rg, _ = _gpu_rhs(numa, dict(cfg, metric_form="nodal"), q, precision)
     err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
-    if precision == "fp64":
+    if precision in FP64_MODES:
         assert err.max() <= TOL_RHS, err
     else:
         assert err[:, 0].max() <= TOL_FP32_RHS, err
@@ -158,7 +158,8 @@ def test_init_state_parity(numa, orc):
     assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
 
 
-@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal")])
+@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal"),
+                                            ("fp64_pairs", "nodal")])
 def test_rk3_100_steps_bubble(numa, orc, precision, form):
     """Workload bubble_4x4x4_N4: 100 SSP-RK3 steps at dt = 0.01 s."""
     w = I.WORKLOADS["bubble_4x4x4_N4"]
@@ -215,9 +216,10 @@ def test_full_size_bubble_rhs(numa, orc):
     q = m.init_state("bubble", I.BUBBLE_PARAMS) + 0.1 * _state(m, cfg, "smooth", seed=21)
     Ro = m.rhs(q)
     floors = rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max())
-    for precision, form in (("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal")):
+    for precision, form in (("fp64", "auto"), ("fp64_pairs", "auto"), ("fp64", "nodal"), ("fp64_pairs", "nodal")):
         Rg, _ = _gpu_rhs(numa, dict(cfg, metric_form=form), q, precision)
         err = rel_errors(Rg, Ro, floors)
+        print(f"full-size RHS {precision} {form}: max rel L2 {err[:, 0].max():.3e}, Linf {err[:, 1].max():.3e}")
         assert err.max() <= TOL_RHS, (precision, form, err)
 
 
