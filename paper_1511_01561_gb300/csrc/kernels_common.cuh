@@ -852,23 +852,27 @@ __device__ __forceinline__ double re_load(const void* re, long long idx) {
 // b = 1: no q^n read, no q^n term); MODE 3 the DSS of the filter correction,
 // q + M^-1 DSS(Jw ((F x F x F) q - q)), with the wall-normal momentum left as
 // it was.
-template <int MODE, bool SHELL, typename RT>
-__device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
-  const long long Ng = a.Ng, Nl = a.Nl;
-  // direct stiffness summation in ascending element-node order (Eq. 4), FP64;
-  // every global node has at least one element node
+// Direct stiffness summation at global node I in ascending element-node
+// order (Eq. 4), FP64; every global node has at least one element node.
+template <typename RT>
+__device__ __forceinline__ void dss_node(const UpdateArgs& a, long long I, double (&s)[5]) {
+  const long long Nl = a.Nl;
   const int t0 = a.off[I], t1 = a.off[I + 1];
   const long long n0 = a.idx[t0];
-  double s0 = re_load<RT>(a.re, n0), s1 = re_load<RT>(a.re, Nl + n0), s2 = re_load<RT>(a.re, 2 * Nl + n0);
-  double s3 = re_load<RT>(a.re, 3 * Nl + n0), s4 = re_load<RT>(a.re, 4 * Nl + n0);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s[v] = re_load<RT>(a.re, v * Nl + n0);
   for (int t = t0 + 1; t < t1; ++t) {
     const long long n = a.idx[t];
-    s0 += re_load<RT>(a.re, n);
-    s1 += re_load<RT>(a.re, Nl + n);
-    s2 += re_load<RT>(a.re, 2 * Nl + n);
-    s3 += re_load<RT>(a.re, 3 * Nl + n);
-    s4 += re_load<RT>(a.re, 4 * Nl + n);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] += re_load<RT>(a.re, v * Nl + n);
   }
+}
+
+// Everything after the DSS at global node I, given its sums s0..s4.
+template <int MODE, bool SHELL>
+__device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long I, double s0, double s1, double s2,
+                                                 double s3, double s4) {
+  const long long Ng = a.Ng;
   const double minv = a.Minv[I];
   const double rp = a.qk[I];
   const uint8_t w = a.wall[I];
@@ -965,9 +969,35 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
 }
 
 template <int MODE, bool SHELL, typename RT>
-__global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
-  const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (I < a.Ng) update_node<MODE, SHELL, RT>(a, I);
+__device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
+  double s[5];
+  dss_node<RT>(a, I, s);
+  update_node_sums<MODE, SHELL>(a, I, s[0], s[1], s[2], s[3], s[4]);
+}
+
+// One block per kDssBlock consecutive global nodes.  The DSS runs in the
+// block's precomputed order (nodes sorted by their number of element nodes,
+// so that the lanes of a warp loop equally often) and leaves the sums in
+// shared memory; the rest runs in natural order (coalesced).  Each node's
+// sum is the same as update_node's, bit for bit.
+template <int MODE, bool SHELL, typename RT>
+__global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
+  __shared__ double sums[5][kDssBlock];
+  const long long base = (long long)blockIdx.x * kDssBlock;
+  {
+    const int lt = a.order[base + threadIdx.x];
+    const long long IA = base + lt;
+    if (IA < a.Ng) {
+      double s[5];
+      dss_node<RT>(a, IA, s);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sums[v][lt] = s[v];
+    }
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const long long I = base + t;
+  if (I < a.Ng) update_node_sums<MODE, SHELL>(a, I, sums[0][t], sums[1][t], sums[2][t], sums[3][t], sums[4][t]);
 }
 
 // ---- ragged multi-member kernels (serving) ---------------------------------

@@ -364,6 +364,23 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
     std::vector<int32_t> fill(m.csr_off.begin(), m.csr_off.end() - 1);
     for (long long n = 0; n < Nl; ++n) m.csr_idx[fill[m.l2g[n]]++] = (int32_t)n;
   }
+  // DSS order: within each block of kDssBlock consecutive global nodes, the
+  // nodes sorted (stably) by their number of element nodes, so that the lanes
+  // of a warp of the update kernel sum the same number of contributions
+  {
+    const long long nb = (Ng + kDssBlock - 1) / kDssBlock;
+    m.dss_order.assign(nb * kDssBlock, 0);
+    std::vector<int> loc(kDssBlock);
+    for (long long b = 0; b < nb; ++b) {
+      const long long I0 = b * kDssBlock;
+      const int n = (int)std::min<long long>(kDssBlock, Ng - I0);
+      std::iota(loc.begin(), loc.end(), 0);
+      std::stable_sort(loc.begin(), loc.begin() + n, [&](int x, int y) {
+        return m.csr_off[I0 + x + 1] - m.csr_off[I0 + x] < m.csr_off[I0 + y + 1] - m.csr_off[I0 + y];
+      });
+      for (int t = 0; t < kDssBlock; ++t) m.dss_order[I0 + t] = (uint8_t)loc[t];
+    }
+  }
   m.Minv.assign(Ng, 0.0);
   for (long long g = 0; g < Ng; ++g) {
     double s = 0.0;

@@ -74,6 +74,7 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   UpdateArgs a;
   a.off = c->L.csr_off;
   a.idx = c->L.csr_idx;
+  a.order = c->L.dss_order;
   a.re = re;
   a.Minv = c->L.Minv;
   a.wall = c->L.wall;
@@ -201,6 +202,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.l2g = (int32_t*)take(Nl * 4);
   d.csr_off = (int32_t*)take((Ng + 1) * 4);
   d.csr_idx = (int32_t*)take(Nl * 4);
+  d.dss_order = (uint8_t*)take((Ng + kDssBlock - 1) / kDssBlock * kDssBlock);
   d.ref = (double*)take(4 * Ng * 8);
   d.Minv = (double*)take(Ng * 8);
   d.wall = (uint8_t*)take(Ng);
@@ -329,6 +331,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
   up(L.csr_idx, m.csr_idx.data(), Nl * 4);
+  up(L.dss_order, m.dss_order.data(), m.dss_order.size());
   up(L.ref, m.ref.data(), 4 * Ng * 8);
   up(L.Minv, m.Minv.data(), Ng * 8);
   up(L.wall, m.wall.data(), Ng);

@@ -14,6 +14,7 @@ namespace numa {
 
 constexpr int kMaxN = 8;
 constexpr int kEosTerms = 12;  // binomial-series terms of (1+x)^gamma - 1 for |x| <= 1/32
+constexpr int kDssBlock = 256;  // threads of the update kernel; the DSS order is sorted within such blocks
 
 // Host-side mesh and geometry (Sec. 2.1: Lobatto points, Eq. 4: Jw and M,
 // Eq. 5: isoparametric metric terms).  Built once per context.
@@ -25,6 +26,8 @@ struct HostMesh {
   std::vector<int32_t> l2g;           // element node -> global node [Nl]
   std::vector<int32_t> csr_off;       // global node -> first entry in csr_idx [Ng+1]
   std::vector<int32_t> csr_idx;       // element nodes of each global node, ascending [Nl]
+  std::vector<uint8_t> dss_order;     // per block of kDssBlock global nodes: local indices sorted by
+                                      // their number of element nodes (stable) [ceil(Ng/kDssBlock)*kDssBlock]
   std::vector<double> met;            // [10][Nl]: dxi_d/dx_c at row 3d+c, then Jw
   std::vector<double> ref;            // [4][Ng]: rho0, (rho theta)_0, p0, 1/(rho theta)_0
   std::vector<double> Minv;           // [Ng]: 1 / sum_e Jw
@@ -61,6 +64,7 @@ struct DevLayout {
   int32_t* l2g = nullptr;
   int32_t* csr_off = nullptr;
   int32_t* csr_idx = nullptr;
+  uint8_t* dss_order = nullptr;  // [ceil(Ng/kDssBlock)*kDssBlock]
   double* ref = nullptr;     // [4][Ng]
   double* Minv = nullptr;    // [Ng]
   uint8_t* wall = nullptr;   // [Ng]
@@ -116,6 +120,7 @@ struct VolumeArgs {
 struct UpdateArgs {
   const int32_t* off;
   const int32_t* idx;
+  const uint8_t* order;  // DSS order within each block of kDssBlock nodes (single-mesh kernel)
   const void* re;
   const double* Minv;
   const uint8_t* wall;

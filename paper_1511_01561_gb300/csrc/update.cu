@@ -43,7 +43,7 @@ cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_
 
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   if (a.Ng == 0) return cudaSuccess;
-  const int nt = 256;
+  const int nt = kDssBlock;  // the kernel's block size: one block per DSS-order block
   const unsigned nb = (unsigned)((a.Ng + nt - 1) / nt);
   const bool f32 = precision == NUMA_FP32_MIXED;
   if (a.mode == 0) {
