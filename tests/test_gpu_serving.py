@@ -32,6 +32,9 @@ REQUESTS = [
     (I.box(4, 4), "bubble", (0.3, 250.0, 450.0, 520.0, 350.0), 0.01, 9, "fp64"),
     (I.shell(2, 1, 3), "jetwave", I.JETWAVE_PARAMS, 1.0, 4, "fp64"),
     (I.box((3, 2, 2), 4), "bubble", (0.8, 250.0, 500.0, 300.0, 300.0), 0.01, 0, "fp32_mixed"),
+    (I.box((2, 2, 3), 4), "bubble", (1.2, 220.0, 480.0, 520.0, 380.0), 0.01, 6, "fp64_pairs"),
+    (I.box(2, 3, warp=0.04), "bubble", I.BUBBLE_PARAMS, 0.01, 5, "fp64_pairs"),
+    (I.box(3, 3, warp=0.03), "bubble", I.BUBBLE_PARAMS, 0.01, 4, "fp64"),
 ]
 
 
