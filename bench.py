@@ -31,7 +31,7 @@ UNIT = "node-updates/s"
 STAGES = 3
 
 
-def parse():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=200)
@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate / saturated request rate")
     p.add_argument("--serve-overload", type=float, default=2.0,
                    help="rate of a second Poisson stream / saturated request rate (0 skips it)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def load_peaks():
@@ -129,6 +129,24 @@ def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float) -> float:
     q^k read, q^{k+1} write, q^n on the stages that use it, the reference
     state (4 doubles) and the primitive-field write (40 or 32 B)."""
     return Nl * (4 + 5 * fp) + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + (40 if fp == 8 else 32))
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    """The largest x over all ranks of the default process group (x itself
+    when there is none); every rank gets the result."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, Ng: int, steps: int, ms: float) -> float:
+    """Node-updates/s per RK stage of `world` replicas that each advanced Ng
+    global nodes by `steps` SSP-RK3 steps, the slowest in `ms` milliseconds."""
+    return world * Ng * STAGES * steps / (ms * 1e-3)
 
 
 class ClockSampler:
@@ -271,12 +289,8 @@ def run_mine(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x: float) -> float:
+        return max_over_ranks(dist, x, dev)
 
     def measure(precision, form="auto"):
         s = numa.Solver(dict(cfg, metric_form=form), precision, device=str(dev))
@@ -292,7 +306,7 @@ def run_mine(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = max_ranks(e0.elapsed_time(e1))
         ck = clocks.stop() if clocks else None
         # per-kernel device times over the same number of steps (event-bracketed launches)
         ms_vol, ms_upd = s.time_kernels(dt, args.steps)
@@ -311,7 +325,7 @@ def run_mine(args):
                 numa.numa_rk_step(s.ctx, dt)
                 numa.numa_get_state(s.ctx, out_host.data_ptr(), False)
             torch.cuda.synchronize(dev)
-            te = max_over_ranks(time.perf_counter() - t0)
+            te = max_ranks(time.perf_counter() - t0)
             e2e = {"value": world * s.Ng * STAGES * args.steps / te, "unit": UNIT,
                    "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
         filt = None
@@ -333,7 +347,7 @@ def run_mine(args):
 
     ms, ms_vol, ms_upd, info, e2e, ck, finite, filt_ms = measure("fp64")
     Ng, Nl, N = info["Ng"], info["Nl"], info["N"]
-    value = world * Ng * STAGES * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, Ng, args.steps, ms)
     nlaunch = STAGES * args.steps
     vol_avg_s = ms_vol * 1e-3 / nlaunch
     flops = volume_flops_per_elem_node(N, affine) * Nl
@@ -512,7 +526,7 @@ def run_serve(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.cpu_worker:
         cpu_worker(args)
     elif args.impl == "reference":
