@@ -717,7 +717,48 @@ void orc_ssprk3_step(long n, double* q, double dt, orc_rhs_fn f, void* ctx, doub
   memcpy(q, qk, sizeof(double) * n);
 }
 
+/* Five-stage, low-storage ("2N") explicit Runge-Kutta of Carpenter and
+ * Kennedy (1994): the paper's integrator has five stages and third order
+ * (Sec. 2.2) but names no coefficients; this scheme has five stages and
+ * order four.  With dq = 0 on entry, for i = 1..5:
+ *   dq <- A_i dq + dt R(q);   q <- q + B_i dq
+ * (A_1 = 0).  work holds 2n doubles. */
+static const double kLsA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kLsB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+
+void orc_lsrk54_coefficients(double* A, double* B) {
+  for (int i = 0; i < 5; ++i) {
+    A[i] = kLsA[i];
+    B[i] = kLsB[i];
+  }
+}
+
+void orc_lsrk54_step(long n, double* q, double dt, orc_rhs_fn f, void* ctx, double* work) {
+  double* dq = work;
+  double* r = work + n;
+  for (long t = 0; t < n; ++t) dq[t] = 0.0;
+  for (int s = 0; s < 5; ++s) {
+    f(ctx, q, r);
+    for (long t = 0; t < n; ++t) {
+      dq[t] = kLsA[s] * dq[t] + dt * r[t];
+      q[t] += kLsB[s] * dq[t];
+    }
+  }
+}
+
 static void numa_rhs_cb(void* ctx, const double* q, double* r) { orc_rhs((const orc_mesh*)ctx, q, r); }
+
+int orc_run_lsrk54(const orc_mesh* m, double* q, double dt, int nsteps) {
+  long n = 5 * m->Ng;
+  double* work = malloc(sizeof(double) * 2 * n);
+  if (!work) return -2;
+  for (int s = 0; s < nsteps; ++s) orc_lsrk54_step(n, q, dt, numa_rhs_cb, (void*)m, work);
+  free(work);
+  return 0;
+}
 
 int orc_run(const orc_mesh* m, double* q, double dt, int nsteps) {
   long n = 5 * m->Ng;

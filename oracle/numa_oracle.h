@@ -96,6 +96,13 @@ void orc_ssprk3_step(long n, double* q, double dt, orc_rhs_fn f, void* ctx, doub
 /* nsteps SSP-RK3 steps of the NUMA system, in place on q. */
 int orc_run(const orc_mesh* m, double* q, double dt, int nsteps);
 
+/* The five-stage low-storage Runge-Kutta scheme (Carpenter-Kennedy, order
+ * four): its coefficients A[5], B[5]; one step on a generic callback (work:
+ * 2n doubles); nsteps steps of the NUMA system in place on q. */
+void orc_lsrk54_coefficients(double* A, double* B);
+void orc_lsrk54_step(long n, double* q, double dt, orc_rhs_fn f, void* ctx, double* work);
+int orc_run_lsrk54(const orc_mesh* m, double* q, double dt, int nsteps);
+
 /* Boyd-Vandeven filter (Sec. 2.3): weights sigma[0..N] of the Legendre modes
  * (first damped mode s, order p, strength mu), the 1D filter matrix
  * F = V diag(sigma) V^-1 (row-major, (N+1)^2), one application of the filter

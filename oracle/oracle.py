@@ -82,6 +82,10 @@ def lib():
         L.orc_ssprk3_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
         L.orc_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
         L.orc_run.restype = ctypes.c_int
+        L.orc_lsrk54_coefficients.argtypes = [dp, dp]
+        L.orc_lsrk54_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
+        L.orc_run_lsrk54.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
+        L.orc_run_lsrk54.restype = ctypes.c_int
         L.orc_filter_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
         L.orc_filter_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
         L.orc_filter_matrix.restype = ctypes.c_int
@@ -175,6 +179,29 @@ def ssprk3_step(q: np.ndarray, dt: float, f) -> np.ndarray:
     return q
 
 
+def lsrk54_step(q: np.ndarray, dt: float, f) -> np.ndarray:
+    """One step of the five-stage low-storage RK of dq/dt = f(q)."""
+    q = np.ascontiguousarray(q, dtype=np.float64).copy()
+    n = q.size
+
+    def cb(_ctx, qp, rp):
+        qa = np.ctypeslib.as_array(qp, shape=(n,))
+        ra = np.ctypeslib.as_array(rp, shape=(n,))
+        ra[:] = f(qa.copy())
+
+    fn = RHS_FN(cb)
+    work = np.zeros(2 * n)
+    lib().orc_lsrk54_step(n, _dp(q), dt, fn, None, _dp(work))
+    return q
+
+
+def lsrk54_coefficients():
+    A = np.zeros(5)
+    B = np.zeros(5)
+    lib().orc_lsrk54_coefficients(_dp(A), _dp(B))
+    return A, B
+
+
 class Mesh:
     """An oracle mesh with its geometry, maps, mass matrix and reference state."""
 
@@ -257,6 +284,13 @@ class Mesh:
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
         rc = lib().orc_run(self._h, _dp(q), dt, nsteps)
         if rc != 0:
+            raise MemoryError("oracle run failed")
+        return q
+
+    def run_lsrk54(self, q: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+        """nsteps steps of the five-stage low-storage RK."""
+        q = np.ascontiguousarray(q, dtype=np.float64).copy()
+        if lib().orc_run_lsrk54(self._h, _dp(q), dt, nsteps) != 0:
             raise MemoryError("oracle run failed")
         return q
 
