@@ -292,15 +292,16 @@ def run_mine(args):
     def max_ranks(x: float) -> float:
         return max_over_ranks(dist, x, dev)
 
-    def measure(precision, form="auto"):
+    def measure(precision, form="auto", scheme="ssp3"):
         s = numa.Solver(dict(cfg, metric_form=form), precision, device=str(dev))
+        s.set_time_scheme(scheme)
         s.init_state(*w["ic"])
         s.run(dt, args.warmup)
         stream = s.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(local) if (precision, form) == ("fp64", "auto") else None
+        clocks = ClockSampler(local) if (precision, form, scheme) == ("fp64", "auto", "ssp3") else None
         e0.record(stream)
         s.run(dt, args.steps)
         e1.record(stream)
@@ -312,7 +313,7 @@ def run_mine(args):
         ms_vol, ms_upd = s.time_kernels(dt, args.steps)
         info = s.info
         e2e = None
-        if not args.no_e2e and (precision, form) == ("fp64", "auto"):
+        if not args.no_e2e and (precision, form, scheme) == ("fp64", "auto", "ssp3"):
             q_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             out_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             s.get_state(q_host)
@@ -329,7 +330,7 @@ def run_mine(args):
             e2e = {"value": world * s.Ng * STAGES * args.steps / te, "unit": UNIT,
                    "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
         filt = None
-        if (precision, form) == ("fp64", "auto") and args.filter_reps > 0:
+        if (precision, form, scheme) == ("fp64", "auto", "ssp3") and args.filter_reps > 0:
             # Boyd-Vandeven filter (element kernel + DSS update), applied on its own
             s.set_filter(0, max(0, w["cfg"]["N"] - 1), 12.0, 1.0)
             s.filter()
@@ -384,6 +385,13 @@ def run_mine(args):
             "element_fp64_tflops_lower_bound": ff / (filt_ms * 1e-3) / 1e12,
             "frac_of_fp64_peak_lower_bound": ff / (filt_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
         }
+    # the five-stage low-storage integrator (the paper's stage count), FP64
+    msl, voll, updl, _, _, _, finl, _ = measure("fp64", "auto", "ls54")
+    line["fp64_ls54"] = {
+        "what": "five-stage low-storage RK (order four) instead of SSP-RK3, same workload and dt",
+        "value": whole_job_rate(world, Ng, args.steps, msl) * 5 / STAGES, "unit": UNIT,
+        "ms_per_step": msl / args.steps, "stages_per_step": 5, "finite": finl,
+        "volume_ms_avg": voll / (5 * args.steps), "update_ms_avg": updl / (5 * args.steps)}
     if affine:
         # the same workload through the per-node form of Eq. 5 (metric terms
         # read and applied at every node), for comparison

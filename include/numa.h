@@ -162,15 +162,31 @@ int numa_rhs(numa_ctx* ctx, const double* q_dev, double* r_dev);
  * GPU race.  q_dev, r_dev: device double[5][Ng], enqueued on the bound stream. */
 int numa_rhs_static_scratch(numa_ctx* ctx, const double* q_dev, double* r_dev);
 
-/* Advance the context's state by one three-stage SSP-RK3 step of size dt
- * (Sec. 2.2 explicit stages: per stage create_rhs, DSS with the inverse mass
- * matrix, update q).  Enqueued on the bound stream; returns without waiting. */
+/* Advance the context's state by one step of size dt of the selected
+ * integrator (numa_set_time_scheme; SSP-RK3 by default; Sec. 2.2 explicit
+ * stages: per stage create_rhs, DSS with the inverse mass matrix, update q).
+ * Enqueued on the bound stream; returns without waiting. */
 int numa_rk_step(numa_ctx* ctx, double dt);
 
-/* nsteps SSP-RK3 steps (one captured CUDA graph per step, replayed), then
+/* nsteps steps of the selected integrator (one captured CUDA graph per step,
+ * replayed), then
  * waits for the stream and returns NUMA_ENONFINITE if any stage produced a
  * non-finite value. */
 int numa_run(numa_ctx* ctx, double dt, int nsteps);
+
+/* Explicit time integrators of numa_rk_step / numa_run (Sec. 2.2).
+ * SSP3: three-stage, third-order strong-stability-preserving RK (Shu-Osher):
+ *   q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1));
+ *   q_new = 1/3 q + 2/3 (q2 + dt R(q2)).
+ * LS54: five-stage, fourth-order low-storage ("2N") RK of Carpenter and
+ *   Kennedy: with dq = 0, for i = 1..5: dq <- A_i dq + dt R(q), q <- q + B_i dq.
+ *   The paper's integrator has five stages and third order but is not
+ *   specified further; this scheme has its stage count and exceeds its order. */
+typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1 } numa_rk_scheme;
+
+/* Select the integrator (default NUMA_RK_SSP3).  NUMA_EINVAL for another
+ * value.  Takes effect at the next step. */
+int numa_set_time_scheme(numa_ctx* ctx, int scheme);
 
 /* Boyd-Vandeven filter (Sec. 2.3), applied as in the time loop of Sec. 6:
  * after every `every`-th step of numa_run / numa_rk_step (the count restarts
@@ -200,7 +216,7 @@ int numa_filter(numa_ctx* ctx);
  * (non-graph) launches, bracketing every kernel with CUDA events on the
  * bound stream, then wait and return the summed device time in ms of the
  * element volume kernels (*ms_volume) and of the DSS/update kernels
- * (*ms_update), 3*nsteps launches each. */
+ * (*ms_update), (stages per step) * nsteps launches each. */
 int numa_time_kernels(numa_ctx* ctx, double dt, int nsteps, double* ms_volume, double* ms_update);
 
 /* Non-finite flag raised by any stage update since the last call; resets it.

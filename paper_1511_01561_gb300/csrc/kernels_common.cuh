@@ -851,7 +851,7 @@ __device__ __forceinline__ double re_load(const void* re, long long idx) {
 // the tendency R; MODE 1 a general RK stage; MODE 2 the first stage (a = 0,
 // b = 1: no q^n read, no q^n term); MODE 3 the DSS of the filter correction,
 // q + M^-1 DSS(Jw ((F x F x F) q - q)), with the wall-normal momentum left as
-// it was.
+// it was; MODE 4 a stage of the low-storage scheme, MODE 5 its first stage.
 // Direct stiffness summation at global node I in ascending element-node
 // order (Eq. 4), FP64; every global node has at least one element node.
 template <typename RT>
@@ -902,7 +902,7 @@ __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long 
     write_prim(a.pa, I, y0, y1, y2, y3, y4);
     return;
   }
-  if constexpr (MODE == 0 || SHELL) {
+  if constexpr (MODE == 0 || MODE >= 4 || SHELL) {
     // R = M^-1 DSS(r_e) + S, then the wall condition
     double R0 = s0 * minv, R1 = s1 * minv, R2 = s2 * minv, R3 = s3 * minv, R4 = s4 * minv;
     if constexpr (SHELL) {
@@ -938,7 +938,25 @@ __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long 
     s3 = R3;
     s4 = R4;
   }
-  if constexpr (MODE >= 1) {
+  if constexpr (MODE >= 4) {
+    // low-storage stage (MODE 5: the first, A = 0): dq <- A dq + dt R,
+    // q <- q + B dq, in place
+    double y[5];
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double Rv = v == 0 ? s0 : v == 1 ? s1 : v == 2 ? s2 : v == 3 ? s3 : s4;
+      double dqv;
+      if constexpr (MODE == 5) dqv = a.dt * Rv;
+      else dqv = fma(a.a, a.dq[v * Ng + I], a.dt * Rv);
+      a.dq[v * Ng + I] = dqv;
+      y[v] = fma(a.b, dqv, v == 0 ? rp : a.qk[v * Ng + I]);
+      a.out[v * Ng + I] = y[v];
+      bad |= nonfinite(y[v]);
+    }
+    if (bad) atomicOr(a.flag, 1);
+    write_prim(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
+  } else if constexpr (MODE >= 1) {
     // q^{k+1} = a q^n + b q^k + b dt R with, in the box, the inverse mass
     // folded into one coefficient: b dt R_v = c s_v (+ b dt S_v), c = b dt / M
     const double c = SHELL ? a.bdt : a.bdt * minv;

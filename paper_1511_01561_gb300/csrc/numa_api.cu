@@ -33,6 +33,12 @@ namespace numa {
 
 const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0};
 const double kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
+// Carpenter and Kennedy's five-stage, fourth-order 2N-storage coefficients
+const double kLsA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kLsB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
 
 PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim) {
   PrimArgs a;
@@ -93,6 +99,7 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   a.bdt = rb * dt;
   a.bdtg = rb * dt * c->cfg.g;
   a.first_stage = (ra == 0.0 && rb == 1.0) ? 1 : 0;
+  a.dq = nullptr;
   a.mode = mode;
   a.flag = c->L.flags;
   a.pa = prim_args(c, nullptr, c->L.prim);
@@ -150,24 +157,40 @@ cudaError_t ensure_prim(numa_ctx* c) {
   return e;
 }
 
-// One SSP-RK3 step on stream s: three times (create_rhs; DSS + M^-1 + update
-// q, which also leaves the primitive fields of the new stage state).  Needs
-// the primitive fields of q^n on entry and leaves those of q^{n+1}.
-// With ev != nullptr every kernel is bracketed by events (12 per step).
+// Stages per step of the context's integrator.
+int rk_stages(const numa_ctx* c) { return c->rk_scheme == NUMA_RK_LS54 ? 5 : 3; }
+
+// One step of the context's integrator on stream s: per stage create_rhs,
+// then DSS + M^-1 + the stage update, which also leaves the primitive fields
+// of the new stage state.  Needs the primitive fields of q^n on entry and
+// leaves those of q^{n+1}.  With ev != nullptr every kernel is bracketed by
+// events (4 per stage).
+//   SSP-RK3: stage states q -> qs -> qs -> q.
+//   low-storage: q updated in place, qs holds dq.
 cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   double* q = c->L.q;
   double* qs = c->L.qs;
+  const bool ls = c->rk_scheme == NUMA_RK_LS54;
   const double* qin[3] = {q, qs, qs};
   double* qout[3] = {qs, qs, q};
-  for (int st = 0; st < 3; ++st) {
+  const int ns = rk_stages(c);
+  for (int st = 0; st < ns; ++st) {
+    const double* qi = ls ? q : qin[st];
     cudaError_t e = ev ? cudaEventRecord(ev[4 * st], s) : cudaSuccess;
-    if (e == cudaSuccess)
-      e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qin[st], c->L.prim, c->L.re), s);
+    if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qi, c->L.prim, c->L.re), s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 1], s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 2], s);
-    if (e == cudaSuccess)
-      e = launch_update(c->cfg.precision, update_args(c, c->L.re, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt),
-                        s);
+    if (e == cudaSuccess) {
+      UpdateArgs ua;
+      if (ls) {
+        ua = update_args(c, c->L.re, q, q, q, 4, kLsA[st], kLsB[st], dt);
+        ua.first_stage = st == 0 ? 1 : 0;
+        ua.dq = qs;
+      } else {
+        ua = update_args(c, c->L.re, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt);
+      }
+      e = launch_update(c->cfg.precision, ua, s);
+    }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 3], s);
     if (e != cudaSuccess) return e;
   }
@@ -492,14 +515,15 @@ int numa_time_kernels(numa_ctx* c, double dt, int nsteps, double* ms_volume, dou
   if (!c || !ms_volume || !ms_update) return NUMA_EINVAL;
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_time_kernels before numa_bind");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NUMA_EINVAL, "bad nsteps or dt");
-  std::vector<cudaEvent_t> ev(12 * (size_t)nsteps, nullptr);
+  const int ns = rk_stages(c);
+  std::vector<cudaEvent_t> ev(4 * (size_t)ns * nsteps, nullptr);
   cudaError_t e = ensure_prim(c);
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
-  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = enqueue_rk_step(c, dt, c->stream, &ev[12 * (size_t)t]);
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = enqueue_rk_step(c, dt, c->stream, &ev[4 * (size_t)ns * t]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   double tv = 0.0, tu = 0.0;
-  for (size_t t = 0; t < 3 * (size_t)nsteps && e == cudaSuccess; ++t) {
+  for (size_t t = 0; t < (size_t)ns * nsteps && e == cudaSuccess; ++t) {
     float a = 0.f, b = 0.f;
     e = cudaEventElapsedTime(&a, ev[4 * t], ev[4 * t + 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * t + 2], ev[4 * t + 3]);
@@ -558,6 +582,17 @@ int numa_set_filter(numa_ctx* c, int every, int s, double p, double mu) {
     cudaError_t e = upload_filter(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "numa_set_filter upload");
   }
+  return NUMA_OK;
+}
+
+int numa_set_time_scheme(numa_ctx* c, int scheme) {
+  if (!c) return NUMA_EINVAL;
+  if (scheme != NUMA_RK_SSP3 && scheme != NUMA_RK_LS54) return fail(c, NUMA_EINVAL, "unknown time scheme");
+  if (scheme != c->rk_scheme && c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->rk_scheme = scheme;
   return NUMA_OK;
 }
 

@@ -134,8 +134,10 @@ struct UpdateArgs {
   double two_omega;    // shell Coriolis 2 Omega
   double a, b, dt;     // out = a qn + b (qk + dt R)
   double bdt, bdtg;    // b dt and b dt g, computed once on the host
-  int first_stage;     // 1 when a = 0 and b = 1 (no q^n term)
-  int mode;            // 0: write R, 1: RK stage, 3: filter DSS (1 and 3 also write the primitives of out)
+  int first_stage;     // 1 when a = 0 and b = 1 (no q^n term); low-storage scheme: A = 0 (no dq read)
+  double* dq;          // low-storage scheme (modes 4, 5): the second register; out = qk = q, a = A_i, b = B_i
+  int mode;            // 0: write R, 1: SSP-RK3 stage, 3: filter DSS, 4: low-storage stage (1, 3, 4 also
+                       // write the primitives of out)
   int* flag;           // non-finite flag
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
 };
@@ -216,6 +218,7 @@ struct numa_ctx {
   const double* graph_q = nullptr;
   // Boyd-Vandeven filter: parameters (set by numa_set_filter), its host
   // matrix, and the steps since it was last applied
+  int rk_scheme = NUMA_RK_SSP3;
   bool filter_set = false;
   int filter_every = 0, filter_s = 0, filter_count = 0;
   double filter_p = 0.0, filter_mu = 0.0;
@@ -229,6 +232,9 @@ namespace numa {
 // SSP-RK3 stage coefficients: q^{k+1} = a_k q^n + b_k (q^k + dt R(q^k))
 extern const double kRkA[3];
 extern const double kRkB[3];
+// five-stage low-storage scheme: dq <- kLsA[i] dq + dt R(q); q <- q + kLsB[i] dq
+extern const double kLsA[5];
+extern const double kLsB[5];
 
 PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim);
 VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, void* re);

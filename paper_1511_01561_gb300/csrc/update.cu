@@ -52,6 +52,14 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
   } else if (a.mode == 3) {
     if (f32) launch_update_m<3, float>(a, nb, nt, s);
     else launch_update_m<3, double>(a, nb, nt, s);
+  } else if (a.mode == 4) {
+    if (a.first_stage) {
+      if (f32) launch_update_m<5, float>(a, nb, nt, s);
+      else launch_update_m<5, double>(a, nb, nt, s);
+    } else {
+      if (f32) launch_update_m<4, float>(a, nb, nt, s);
+      else launch_update_m<4, double>(a, nb, nt, s);
+    }
   } else if (a.first_stage) {
     if (f32) launch_update_m<2, float>(a, nb, nt, s);
     else launch_update_m<2, double>(a, nb, nt, s);

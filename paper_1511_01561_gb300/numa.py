@@ -68,6 +68,7 @@ def _load():
         "numa_rk_step": [vp, d],
         "numa_run": [vp, d, i],
         "numa_set_filter": [vp, i, i, d, d],
+        "numa_set_time_scheme": [vp, i],
         "numa_filter": [vp],
         "numa_check_finite": [vp, ctypes.POINTER(i)],
         "numa_time_kernels": [vp, d, i, dp, dp],
@@ -178,6 +179,13 @@ def numa_run(ctx, dt: float, nsteps: int) -> None:
     _check(ctx, lib.numa_run(ctx, dt, nsteps))
 
 
+RK_SCHEME = {"ssp3": 0, "ls54": 1}
+
+
+def numa_set_time_scheme(ctx, scheme: str) -> None:
+    _check(ctx, lib.numa_set_time_scheme(ctx, RK_SCHEME[scheme]))
+
+
 def numa_set_filter(ctx, every: int, s: int, p: float, mu: float = 1.0) -> None:
     _check(ctx, lib.numa_set_filter(ctx, int(every), int(s), float(p), float(mu)))
 
@@ -286,6 +294,11 @@ class Solver:
 
     def run(self, dt: float, nsteps: int):
         numa_run(self.ctx, dt, nsteps)
+
+    def set_time_scheme(self, scheme: str):
+        """"ssp3" (three-stage SSP-RK3, the default) or "ls54" (five-stage
+        low-storage RK of order four)."""
+        numa_set_time_scheme(self.ctx, scheme)
 
     def set_filter(self, every: int, s: int, p: float, mu: float = 1.0):
         """Boyd-Vandeven filter after every `every`-th step (0: off)."""

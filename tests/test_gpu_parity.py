@@ -293,3 +293,53 @@ def test_fp32_mixed_100_steps(numa, orc):
         s.close()
     err = rel_errors(qg, qo, state_floors(qo, m.ref()[0].max()))
     assert err[:, 0].max() <= 1e-4, err
+
+
+# ------------------------------------ five-stage low-storage integrator ----
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_100), ("fp64_pairs", TOL_100), ("fp32_mixed", 1e-4)])
+def test_lsrk54_100_steps_bubble(numa, orc, precision, tol):
+    """100 steps of the five-stage low-storage RK on bubble_4x4x4_N4."""
+    w = I.WORKLOADS["bubble_4x4x4_N4"]
+    m = orc.Mesh(w["cfg"])
+    q0 = m.init_state(*w["ic"])
+    qo = m.run_lsrk54(q0, w["dt"], w["steps"])
+    s = numa.Solver(w["cfg"], precision)
+    try:
+        s.set_time_scheme("ls54")
+        s.set_state(q0)
+        s.run(w["dt"], w["steps"])
+        qg = s.get_state().numpy().copy()
+        s.set_state(q0)
+        for _ in range(w["steps"]):
+            s.rk_step(w["dt"])
+        qg2 = s.get_state().numpy()
+    finally:
+        s.close()
+    assert np.array_equal(qg, qg2)
+    err = rel_errors(qg, qo, state_floors(qo, m.ref()[0].max()))
+    assert (err if precision in FP64_MODES else err[:, 0]).max() <= tol, err
+    # a different integrator: the SSP-RK3 result differs by more than the bar
+    assert np.abs(qo - m.run(q0, w["dt"], w["steps"])).max() > 0.0
+
+
+def test_lsrk54_shell(numa, orc):
+    cfg, dt, steps = I.shell(2, 2, 3), 2.0, 12
+    m = orc.Mesh(cfg)
+    q0 = 0.3 * _state(m, cfg, "smooth", seed=9) + m.init_state("jetwave", I.JETWAVE_PARAMS)
+    rhat = m.coords() / np.linalg.norm(m.coords(), axis=0)
+    walls = (m.wall() & 8) != 0
+    q0[1:4, walls] -= (q0[1:4, walls] * rhat[:, walls]).sum(0) * rhat[:, walls]
+    qo = m.run_lsrk54(q0, dt, steps)
+    s = numa.Solver(cfg, "fp64")
+    try:
+        perm = match_nodes(s.coords(), m.coords(), tol=1e-3)
+        s.set_time_scheme("ls54")
+        s.set_state(np.ascontiguousarray(q0[:, perm]))
+        s.run(dt, steps)
+        qg = s.get_state().numpy()
+    finally:
+        s.close()
+    qr = qo[:, perm]
+    err = rel_errors(qg, qr, state_floors(qr, m.ref()[0].max()))
+    assert err.max() <= TOL_100, err
