@@ -146,7 +146,6 @@ __device__ __forceinline__ Pairs pp_sub(Pairs a, Pairs b) {
 }
 
 __device__ __noinline__ double eos_ratio_rare(double x, double gamma) { return expm1(gamma * log1p(x)); }
-__device__ __noinline__ float eos_ratio_f_rare(float x, float gamma) { return expm1f(gamma * log1pf(x)); }
 
 // (1+x)^gamma - 1 with full relative accuracy: the binomial series
 // sum_k C(gamma,k) x^k (Horner), 6 terms for |x| <= 2^-10 and 12 terms for
@@ -159,14 +158,6 @@ __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
   const int K = hx <= 0x3f500000u ? 6 : kEosTerms;                   // |x| <= 2^-10 : 6 terms
   double t = a.eos[K - 1];
   for (int k = K - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
-  return t * x;
-}
-
-__device__ __forceinline__ float eos_ratio_f(float x, const PrimArgs& a) {
-  if (fabsf(x) > 0.03125f) return eos_ratio_f_rare(x, a.gammaf);
-  float t = a.eosf[6];
-#pragma unroll
-  for (int k = 5; k >= 0; --k) t = fmaf(t, x, a.eosf[k]);
   return t * x;
 }
 
@@ -191,7 +182,7 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     w[4 * Ng + I] = Uyf * rf;
     w[5 * Ng + I] = Uzf * rf;
     w[6 * Ng + I] = d2f(Th) * rf;
-    w[7 * Ng + I] = d2f(p0) * eos_ratio_f(d2f(Tp) * d2f(iTh0), a);
+    w[7 * Ng + I] = d2f(p0 * eos_ratio(Tp * iTh0, a));  // p' stays FP64 until stored
   } else if (a.precision == NUMA_FP64_PAIRS) {
     // FP64 primitives, stored as (hi, lo) pairs for the element kernel
     Pairs* w = static_cast<Pairs*>(a.prim);

@@ -48,11 +48,7 @@ PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim) {
   a.Ng = c->mesh.Ng;
   a.precision = c->cfg.precision;
   a.gamma = c->gamma;
-  a.gammaf = (float)c->gamma;
-  for (int k = 0; k < kEosTerms; ++k) {
-    a.eos[k] = c->eos[k];
-    a.eosf[k] = (float)c->eos[k];
-  }
+  for (int k = 0; k < kEosTerms; ++k) a.eos[k] = c->eos[k];
   return a;
 }
 

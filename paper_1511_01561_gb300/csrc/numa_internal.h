@@ -91,8 +91,6 @@ struct PrimArgs {
   int precision;
   double gamma;
   double eos[kEosTerms];  // binomial coefficients C(gamma, k), k = 1..kEosTerms
-  float gammaf;           // the same in FP32 for the FP32 form (rounded once, on the host)
-  float eosf[kEosTerms];
 };
 
 // Every element of the mesh maps affinely onto the reference cube (a box
