@@ -378,3 +378,20 @@ def test_full_size_shell_rhs(numa, orc):
             assert err[:, 0].max() <= TOL_RHS and err[:, 1].max() <= 3e-12, (precision, err)
         else:
             assert err.max() <= TOL_RHS, (precision, err)
+
+
+@pytest.mark.slow
+def test_largest_serving_member_rhs(numa, orc):
+    """The largest request of the serving workload, a 48^3-element box at N=6
+    (24.1M global nodes, 37.9M element nodes): the full FP64 RHS against the
+    oracle, which exercises the index arithmetic at the largest size served."""
+    cfg = I.box(48, 6)
+    m = orc.Mesh(cfg)
+    assert m.Ng == 289**3
+    q = m.init_state("bubble", (1.5, 200.0, 450.0, 550.0, 400.0))
+    q += 0.05 * scaled_random_state(m.Ng, *m.ref()[:2], seed=48)
+    Ro = m.rhs(q)
+    Rg, _ = _gpu_rhs(numa, cfg, q, "fp64")
+    err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
+    print(f"48^3 N=6 RHS fp64: max rel L2 {err[:, 0].max():.3e}, Linf {err[:, 1].max():.3e}")
+    assert err.max() <= TOL_RHS, err
