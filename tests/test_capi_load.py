@@ -107,6 +107,9 @@ def test_argument_errors_without_gpu(numa):
         with pytest.raises(numa.NumaError) as e:
             numa.numa_filter(ctx)
         assert e.value.code == -7  # not bound
+        numa.numa_set_time_scheme(ctx, "ls54")
+        numa.numa_set_time_scheme(ctx, "ssp3")
+        assert numa.lib.numa_set_time_scheme(ctx, 7) == -1
     finally:
         numa.numa_destroy(ctx)
     assert numa.lib.numa_destroy(None) == -1

@@ -114,3 +114,31 @@ def test_filter_errors(numa):
             assert e.value.code == -1
     finally:
         sv.close()
+
+
+def test_filter_set_before_bind(numa, orc):
+    """A filter configured before numa_bind is uploaded by the bind."""
+    torch = pytest.importorskip("torch")
+    cfg = I.box(2, 3)
+    m = orc.Mesh(cfg)
+    rho0, th0, _ = m.ref()
+    q = scaled_random_state(m.Ng, rho0, th0, seed=17)
+    ref = m.filter(q, 2, P_ORDER, 0.6)
+    ctx = numa.numa_create(cfg)
+    try:
+        numa.numa_set_filter(ctx, 0, 2, P_ORDER, 0.6)
+        info = numa.numa_get_mesh_info(ctx)
+        ws = torch.empty(info["workspace_bytes"] + 256, dtype=torch.uint8, device="cuda")
+        base = (ws.data_ptr() + 255) // 256 * 256
+        stream = torch.cuda.current_stream()
+        numa.numa_bind(ctx, base, info["workspace_bytes"], stream.cuda_stream)
+        qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+        numa.numa_set_state(ctx, qd.data_ptr(), True)
+        numa.numa_filter(ctx)
+        out = torch.empty_like(qd)
+        numa.numa_get_state(ctx, out.data_ptr(), True)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+    finally:
+        numa.numa_destroy(ctx)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(q).max()
