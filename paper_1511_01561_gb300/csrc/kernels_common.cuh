@@ -152,10 +152,14 @@ __device__ __noinline__ double eos_ratio_rare(double x, double gamma) { return e
 // |x| <= 2^-5 (truncation below 1e-17 relative in both), else
 // expm1(gamma log1p(x)).  The term count is a loop bound, not a branch, so
 // that the two series are never both issued.
+template <bool F32OUT = false>
 __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
   const unsigned hx = ((unsigned)__double2hiint(x)) & 0x7fffffffu;  // |x| by its high word
   if (hx > 0x3fa00000u) return eos_ratio_rare(x, a.gamma);          // |x| > 2^-5
-  const int K = hx <= 0x3f500000u ? 6 : kEosTerms;                   // |x| <= 2^-10 : 6 terms
+  // relative truncation about |x|^K: below 2^-53 with 6 (|x| <= 2^-10) or 12
+  // (|x| <= 2^-5) terms; for a result stored as a float (F32OUT), below 2^-26
+  // with 3 or 6 terms
+  const int K = hx <= 0x3f500000u ? (F32OUT ? 3 : 6) : (F32OUT ? 6 : kEosTerms);
   double t = a.eos[K - 1];
   for (int k = K - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
   return t * x;
@@ -168,12 +172,12 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
                                            double Uz, double Tp) {
   const long long Ng = a.Ng;
   const double rho0 = a.ref[I], Th0 = a.ref[Ng + I], p0 = a.ref[2 * Ng + I], iTh0 = a.ref[3 * Ng + I];
-  const double rho = rho0 + rp;
-  const double Th = Th0 + Tp;
   if (a.precision == NUMA_FP32_MIXED) {
-    // reference + perturbation in FP64, the rest in FP32
+    // u and theta are FP32 fields, so rho and Theta are summed in FP32; p'
+    // (the reference-state subtraction of the equation of state) in FP64, to
+    // the accuracy of the float it is stored as
     float* w = static_cast<float*>(a.prim);
-    const float rf = 1.0f / d2f(rho);
+    const float rf = 1.0f / (d2f(rho0) + d2f(rp));
     const float Uxf = d2f(Ux), Uyf = d2f(Uy), Uzf = d2f(Uz);
     w[I] = Uxf;
     w[Ng + I] = Uyf;
@@ -181,9 +185,13 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     w[3 * Ng + I] = Uxf * rf;
     w[4 * Ng + I] = Uyf * rf;
     w[5 * Ng + I] = Uzf * rf;
-    w[6 * Ng + I] = d2f(Th) * rf;
-    w[7 * Ng + I] = d2f(p0 * eos_ratio(Tp * iTh0, a));  // p' stays FP64 until stored
-  } else if (a.precision == NUMA_FP64_PAIRS) {
+    w[6 * Ng + I] = (d2f(Th0) + d2f(Tp)) * rf;
+    w[7 * Ng + I] = d2f(p0 * eos_ratio<true>(Tp * iTh0, a));
+    return;
+  }
+  const double rho = rho0 + rp;
+  const double Th = Th0 + Tp;
+  if (a.precision == NUMA_FP64_PAIRS) {
     // FP64 primitives, stored as (hi, lo) pairs for the element kernel
     Pairs* w = static_cast<Pairs*>(a.prim);
     const double r = rcp64(rho);
