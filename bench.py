@@ -72,12 +72,12 @@ FP64_PEAK_TFLOPS = 1.25
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "cd526a34308af0f4",
-               "volume_fp64_affine": 224.382464e6 + 126.305792e6,
-               "volume_fp64_nodal": 481.538048e6 + 142.449152e6,
-               "volume_fp32_affine": 139.237888e6 + 53.951488e6,
-               "volume_fp32_nodal": 248.957440e6 + 63.060992e6,
-               "volume_pairs_affine": 224.357888e6 + 129.075456e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "7b9df404c5aebd61",
+               "volume_fp64_affine": 224.309760e6 + 126.261248e6,
+               "volume_fp64_nodal": 481.487104e6 + 142.893312e6,
+               "volume_fp32_affine": 139.259136e6 + 53.536512e6,
+               "volume_fp32_nodal": 248.957696e6 + 62.950656e6,
+               "volume_pairs_affine": 224.520448e6 + 129.159424e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
