@@ -395,3 +395,21 @@ def test_largest_serving_member_rhs(numa, orc):
     err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
     print(f"48^3 N=6 RHS fp64: max rel L2 {err[:, 0].max():.3e}, Linf {err[:, 1].max():.3e}")
     assert err.max() <= TOL_RHS, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_pairs", "fp32_mixed"])
+def test_rhs_parity_large_theta_perturbation(numa, orc, precision):
+    """Theta' up to 5% of (rho theta)_0: the equation of state leaves the
+    binomial series (|x| > 2^-5) for expm1(gamma log1p(x)) at many nodes."""
+    cfg = I.box((3, 2, 2), 4)
+    m = orc.Mesh(cfg)
+    rho0, th0, _ = m.ref()
+    q = scaled_random_state(m.Ng, rho0, th0, seed=55, rel=0.05)
+    assert (np.abs(q[4] / th0) > 2.0**-5).mean() > 0.2
+    Ro = m.rhs(q)
+    Rg, _ = _gpu_rhs(numa, cfg, q, precision)
+    err = rel_errors(Rg, Ro, rhs_floors(Ro, m.ref()[0].max(), _dx_min(cfg, m), np.abs(q[1:4]).max()))
+    if precision == "fp32_mixed":
+        assert err[:, 0].max() <= TOL_FP32_RHS, err
+    else:
+        assert err.max() <= TOL_RHS, err
