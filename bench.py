@@ -72,12 +72,12 @@ FP64_PEAK_TFLOPS = 1.25
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "7b9df404c5aebd61",
-               "volume_fp64_affine": 224.309760e6 + 126.261248e6,
-               "volume_fp64_nodal": 481.487104e6 + 142.893312e6,
-               "volume_fp32_affine": 139.259136e6 + 53.536512e6,
-               "volume_fp32_nodal": 248.957696e6 + 62.950656e6,
-               "volume_pairs_affine": 224.520448e6 + 129.159424e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "fd055b861f803b9f",
+               "volume_fp64_affine": 224.358912e6 + 126.825216e6,
+               "volume_fp64_nodal": 481.542400e6 + 142.580992e6,
+               "volume_fp32_affine": 139.276288e6 + 53.992960e6,
+               "volume_fp32_nodal": 248.955392e6 + 63.062272e6,
+               "volume_pairs_affine": 224.357120e6 + 129.257472e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 

@@ -84,11 +84,11 @@ cudaError_t launch_filter_t(const FilterArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
   constexpr size_t smem = sizeof(T) * (10 * NP + P * P);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static DeviceFlags attr_set;
+  if (!attr_set.has()) {
     cudaError_t e = cudaFuncSetAttribute(filter_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.set();
   }
   if (a.Ne == 0) return cudaSuccess;
   filter_kernel<N, T><<<a.Ne, NT, smem, s>>>(a);

@@ -11,6 +11,7 @@
 // finiteness test are done with integer operations on the bit patterns.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
@@ -1070,17 +1071,50 @@ __global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restric
   }
 }
 
+// Kernel attributes (the dynamic shared-memory limit) apply per device, so a
+// launch template records per device (one bit each, up to 64) that it has
+// set them there.  The bit is set after the attribute call succeeds: two
+// host threads may both set an attribute, but none launches before it is set.
+class DeviceFlags {
+ public:
+  bool has() const { return (bits_.load() >> device()) & 1ull; }
+  void set() { bits_.fetch_or(1ull << device()); }
+
+ private:
+  static int device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    return dev & 63;
+  }
+  std::atomic<unsigned long long> bits_{0};
+};
+
+// A per-device value computed once (SM count, persistent grid size).
+class DeviceInts {
+ public:
+  int get() const { return v_[device()].load(); }
+  void put(int x) { v_[device()].store(x); }
+
+ private:
+  static int device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    return dev & 63;
+  }
+  std::atomic<int> v_[64] = {};
+};
+
 template <int N, typename T, bool AFF>
 cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
   const size_t smem = element_smem_bytes<N, T, AFF>();
-  static bool attr_set = false;
-  if (!attr_set) {
+  static DeviceFlags attr_set;
+  if (!attr_set.has()) {
     cudaError_t e =
         cudaFuncSetAttribute(volume_kernel<N, T, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.set();
   }
   if (a.Ne == 0) return cudaSuccess;
   volume_kernel<N, T, AFF><<<a.Ne, NT, smem, s>>>(a);
@@ -1104,12 +1138,15 @@ cudaError_t launch_volume_p(int N, const VolumeArgs& a, cudaStream_t s) {
 
 
 
+// SMs of the current device.
 int sm_count() {
-  static int n = 0;
+  static DeviceInts count;
+  int n = count.get();
   if (!n) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       n = 1;
+    count.put(n);
   }
   return n;
 }
@@ -1120,7 +1157,8 @@ cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cu
   constexpr int P = N + 1, NP = P * P * P;
   constexpr int NT = (NP + 31) / 32 * 32;
   const size_t smem = element_smem_bytes<N, T, AFF>();
-  static int grid = 0;
+  static DeviceInts grids;  // per device, set up at its first launch there
+  int grid = grids.get();
   if (!grid) {
     cudaError_t e =
         cudaFuncSetAttribute(volume_ragged<N, T, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1129,6 +1167,7 @@ cudaError_t launch_volume_ragged_t(const MemberDesc* d, const RaggedGroup* g, cu
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, volume_ragged<N, T, AFF>, NT, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * sm_count();
+    grids.put(grid);
   }
   volume_ragged<N, T, AFF><<<grid, NT, smem, s>>>(d, g);
   return cudaGetLastError();
