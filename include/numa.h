@@ -15,6 +15,13 @@
  *     device; "host" pointers are read or written before the call returns
  *     unless stated otherwise.
  *
+ * Devices and threads
+ *   A context works on the device that is current when numa_bind is called;
+ *   calls on it must be made with that device current.  Contexts on
+ *   different devices may be used from one process.  A context is not
+ *   thread-safe: calls on one context must not overlap.  Calls on different
+ *   contexts may come from different threads.
+ *
  * Errors
  *   Every call returns an int status: NUMA_OK (0) or a negative NUMA_E* code.
  *   Nothing aborts, traps or exits.  numa_last_error() returns a message owned
