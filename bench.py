@@ -41,6 +41,7 @@ def parse_args(argv=None):
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 mixed-precision line")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-dg", action="store_true", help="skip the DG-storage comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--filter-reps", type=int, default=20, help="filter applications timed (0 skips)")
@@ -123,12 +124,15 @@ def volume_bytes(Nl: int, Ng: int, fp: int, N: int = 4, affine: bool = False) ->
     return Nl * (10 * fp + 4 + 5 * fp) + Ng * 8 * fp
 
 
-def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float) -> float:
+def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float, entries: int = None) -> float:
     """Algorithmic DRAM bytes of one DSS/update launch: CSR (4 B per entry +
-    4 B per node), residual read (5 values per element node), M^-1, wall flag,
-    q^k read, q^{k+1} write, q^n on the stages that use it, the reference
-    state (4 doubles) and the primitive-field write (40 or 32 B)."""
-    return Nl * (4 + 5 * fp) + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + (40 if fp == 8 else 32))
+    4 B per node; `entries` = Nl unless given), residual read (5 values per
+    element node, once), M^-1, wall flag, q^k read, q^{k+1} write, q^n on the
+    stages that use it, the reference state (4 doubles) and the
+    primitive-field write (40 or 32 B)."""
+    entries = Nl if entries is None else entries
+    return (entries * 4 + Nl * 5 * fp
+            + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + (40 if fp == 8 else 32)))
 
 
 def max_over_ranks(dist, x: float, device=None) -> float:
@@ -302,8 +306,8 @@ def run_mine(args):
     def max_ranks(x: float) -> float:
         return max_over_ranks(dist, x, dev)
 
-    def measure(precision, form="auto", scheme="ssp3"):
-        s = numa.Solver(dict(cfg, metric_form=form), precision, device=str(dev))
+    def measure(precision, form="auto", scheme="ssp3", storage="cg"):
+        s = numa.Solver(dict(cfg, metric_form=form, storage=storage), precision, device=str(dev))
         s.set_time_scheme(scheme)
         s.init_state(*w["ic"])
         s.run(dt, args.warmup)
@@ -458,6 +462,23 @@ def run_mine(args):
             line["fp64_pairs"]["nodal_form"] = {
                 "value": world * Ng * STAGES * args.steps / (mspn * 1e-3), "ms_per_step": mspn / args.steps,
                 "finite": finpn, "volume_ms_avg": volpn / nlaunch}
+    if not args.no_dg:
+        # DG storage of the node data (one copy per element node) against CG
+        # storage, same workload; rates count the CG global nodes advanced
+        line["storage_dg"] = {"what": "DG storage (one value per element node) instead of CG storage, "
+                                      "same workload and dt; value counts CG global nodes", "unit": UNIT}
+        for prec, fp, ref_v in (("fp64", 8, value), ("fp32_mixed", 4, line.get("fp32_mixed", {}).get("value"))):
+            if prec == "fp32_mixed" and args.no_fp32:
+                continue
+            msd, vold, updd, infod, _, _, find, _ = measure(prec, "auto", "ssp3", "dg")
+            vd = whole_job_rate(world, Ng, args.steps, msd)
+            upd_s = updd * 1e-3 / nlaunch
+            line["storage_dg"][prec] = {
+                "value": vd, "ms_per_step": msd / args.steps, "vs_cg_storage": vd / ref_v if ref_v else None,
+                "storage_nodes": infod["Ng"], "dss_entries": infod["dss_entries"], "finite": find,
+                "volume_ms_avg": vold / nlaunch, "update_ms_avg": 1e3 * upd_s,
+                "update_hbm_frac": update_bytes(Nl, infod["Ng"], fp, 2 / 3, infod["dss_entries"])
+                / upd_s / 1e9 / hbm_gbs}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -88,6 +88,17 @@ enum numa_ic_kind { NUMA_IC_REST = 0, NUMA_IC_BUBBLE = 1, NUMA_IC_UNIFORM = 2, N
  *   applied after the derivative). */
 typedef enum { NUMA_METRIC_AUTO = 0, NUMA_METRIC_NODAL = 1 } numa_metric_form;
 
+/* Storage of the node data (Sec. 5's comparison of CG and DG storage).
+ * CG: one value per global node; element nodes that coincide share it and
+ *   the element kernel gathers through the element-to-global map.
+ * DG: one value per element node (Ng = Nl in numa_mesh_info): every element
+ *   keeps its own copy of its nodes.  DSS still sums over all element nodes
+ *   at the same point, in the same ascending order as CG storage does, so
+ *   every copy holds the value CG storage holds at that point, bitwise; the
+ *   state arrays, coordinates and get/set_state use the Nl storage nodes in
+ *   element order.  The serving calls (numa_sched_submit) take CG only. */
+typedef enum { NUMA_STORAGE_CG = 0, NUMA_STORAGE_DG = 1 } numa_storage;
+
 typedef struct {
   int mesh_kind;           /* numa_mesh_kind */
   int N;                   /* polynomial order, 1..8 (N+1 LGL points per direction) */
@@ -108,12 +119,17 @@ typedef struct {
   double theta0, T0;       /* isentropic potential temperature / isothermal temperature */
   int precision;           /* numa_precision */
   int metric_form;         /* numa_metric_form: how the element kernel applies the metric terms */
+  int storage;             /* numa_storage: CG (0, default) or DG storage of the node data */
 } numa_config;
 
 typedef struct {
-  long long Ne, Nl, Ng;   /* elements, element-local nodes Ne (N+1)^3, global nodes */
+  long long Ne, Nl, Ng;   /* elements, element-local nodes Ne (N+1)^3, storage nodes
+                             (global nodes for CG storage, Nl for DG storage) */
   size_t workspace_bytes; /* device bytes numa_bind needs */
   int N;
+  long long dss_entries;  /* element residuals the DSS reads per stage: Nl for CG storage;
+                             for DG storage every copy reads all residuals at its point,
+                             the sum over global nodes of (element nodes there)^2 */
 } numa_mesh_info;
 
 typedef struct numa_ctx numa_ctx;

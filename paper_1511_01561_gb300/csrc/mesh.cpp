@@ -212,6 +212,25 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
   }
 }
 
+// DSS order: within each block of kDssBlock consecutive global nodes, the
+// nodes sorted (stably) by their number of element nodes, so that the lanes
+// of a warp of the update kernel sum the same number of contributions.
+void build_dss_order(HostMesh& m) {
+  const long long Ng = m.Ng;
+  const long long nb = (Ng + kDssBlock - 1) / kDssBlock;
+  m.dss_order.assign(nb * kDssBlock, 0);
+  std::vector<int> loc(kDssBlock);
+  for (long long b = 0; b < nb; ++b) {
+    const long long I0 = b * kDssBlock;
+    const int n = (int)std::min<long long>(kDssBlock, Ng - I0);
+    std::iota(loc.begin(), loc.end(), 0);
+    std::stable_sort(loc.begin(), loc.begin() + n, [&](int x, int y) {
+      return m.csr_off[I0 + x + 1] - m.csr_off[I0 + x] < m.csr_off[I0 + y + 1] - m.csr_off[I0 + y];
+    });
+    for (int t = 0; t < kDssBlock; ++t) m.dss_order[I0 + t] = (uint8_t)loc[t];
+  }
+}
+
 }  // namespace
 
 // Boyd-Vandeven filter (Sec. 2.3).  Weight of Legendre mode k: 1 below the
@@ -364,23 +383,8 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
     std::vector<int32_t> fill(m.csr_off.begin(), m.csr_off.end() - 1);
     for (long long n = 0; n < Nl; ++n) m.csr_idx[fill[m.l2g[n]]++] = (int32_t)n;
   }
-  // DSS order: within each block of kDssBlock consecutive global nodes, the
-  // nodes sorted (stably) by their number of element nodes, so that the lanes
-  // of a warp of the update kernel sum the same number of contributions
-  {
-    const long long nb = (Ng + kDssBlock - 1) / kDssBlock;
-    m.dss_order.assign(nb * kDssBlock, 0);
-    std::vector<int> loc(kDssBlock);
-    for (long long b = 0; b < nb; ++b) {
-      const long long I0 = b * kDssBlock;
-      const int n = (int)std::min<long long>(kDssBlock, Ng - I0);
-      std::iota(loc.begin(), loc.end(), 0);
-      std::stable_sort(loc.begin(), loc.begin() + n, [&](int x, int y) {
-        return m.csr_off[I0 + x + 1] - m.csr_off[I0 + x] < m.csr_off[I0 + y + 1] - m.csr_off[I0 + y];
-      });
-      for (int t = 0; t < kDssBlock; ++t) m.dss_order[I0 + t] = (uint8_t)loc[t];
-    }
-  }
+  m.nentries = Nl;
+  build_dss_order(m);
   m.Minv.assign(Ng, 0.0);
   for (long long g = 0; g < Ng; ++g) {
     double s = 0.0;
@@ -435,6 +439,48 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
     m.ref[3 * Ng + g] = 1.0 / Th0;
   }
   return true;
+}
+
+// DG storage (the paper's Sec. 5 comparison of CG, DG and CG/DG storage):
+// every element node keeps its own copy of the node data.  The expanded mesh
+// has Nl storage nodes, l2g the identity, and per-node arrays (coordinates,
+// reference state, M^-1, wall flags, shell vectors) copied from each element
+// node's global node.  Storage node n's DSS entries are those of its global
+// node g = l2g[n] (all element nodes at g, ascending), so every copy forms the
+// same sum, in the same order, as CG storage forms at g.
+void expand_to_dg_storage(HostMesh& m) {
+  const long long Nl = m.Nl, Ng = m.Ng;
+  const std::vector<int32_t> g_of = m.l2g;
+  auto expand = [&](std::vector<double>& v, int rows) {
+    if (v.empty()) return;
+    std::vector<double> out((size_t)rows * Nl);
+    for (int r = 0; r < rows; ++r)
+      for (long long n = 0; n < Nl; ++n) out[r * Nl + n] = v[r * Ng + g_of[n]];
+    v.swap(out);
+  };
+  expand(m.gxyz, 3);
+  expand(m.ref, 4);
+  expand(m.Minv, 1);
+  expand(m.gvec, 3);
+  expand(m.nrm, 3);
+  {
+    std::vector<uint8_t> w(Nl);
+    for (long long n = 0; n < Nl; ++n) w[n] = m.wall[g_of[n]];
+    m.wall.swap(w);
+  }
+  std::vector<int32_t> off(Nl + 1, 0), idx;
+  for (long long n = 0; n < Nl; ++n) off[n + 1] = off[n] + (m.csr_off[g_of[n] + 1] - m.csr_off[g_of[n]]);
+  idx.resize(off[Nl]);
+  for (long long n = 0; n < Nl; ++n) {
+    const int32_t t0 = m.csr_off[g_of[n]], t1 = m.csr_off[g_of[n] + 1];
+    std::copy(m.csr_idx.begin() + t0, m.csr_idx.begin() + t1, idx.begin() + off[n]);
+  }
+  m.csr_off.swap(off);
+  m.csr_idx.swap(idx);
+  m.nentries = (long long)m.csr_idx.size();
+  std::iota(m.l2g.begin(), m.l2g.end(), 0);
+  m.Ng = Nl;
+  build_dss_order(m);
 }
 
 bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const double* prm, int nprm,

@@ -220,7 +220,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   else d.met64 = (double*)take(10 * Nl * 8);
   d.l2g = (int32_t*)take(Nl * 4);
   d.csr_off = (int32_t*)take((Ng + 1) * 4);
-  d.csr_idx = (int32_t*)take(Nl * 4);
+  d.csr_idx = (int32_t*)take((size_t)m.nentries * 4);
   d.dss_order = (uint8_t*)take((Ng + kDssBlock - 1) / kDssBlock * kDssBlock);
   d.ref = (double*)take(4 * Ng * 8);
   d.Minv = (double*)take(Ng * 8);
@@ -269,6 +269,7 @@ int numa_create(const numa_config* cfg, numa_ctx** out) {
   if (cfg->precision != NUMA_FP64 && cfg->precision != NUMA_FP32_MIXED && cfg->precision != NUMA_FP64_PAIRS)
     return NUMA_EINVAL;
   if (cfg->metric_form != NUMA_METRIC_AUTO && cfg->metric_form != NUMA_METRIC_NODAL) return NUMA_EINVAL;
+  if (cfg->storage != NUMA_STORAGE_CG && cfg->storage != NUMA_STORAGE_DG) return NUMA_EINVAL;
   if (!(cfg->cv > 0) || !(cfg->cp > cfg->cv) || !(cfg->Rd > 0) || !(cfg->P00 > 0)) return NUMA_EINVAL;
   numa_ctx* c = new (std::nothrow) numa_ctx();
   if (!c) return NUMA_ENOMEM;
@@ -285,6 +286,13 @@ int numa_create(const numa_config* cfg, numa_ctx** out) {
       delete c;
       return NUMA_EINVAL;
     }
+    if (cfg->storage == NUMA_STORAGE_DG) {
+      if (c->mesh.Nl * 8 > 0x7fffffffLL) {  // DG CSR entries stay below 2^31 (at most 8 per node)
+        delete c;
+        return NUMA_EINVAL;
+      }
+      expand_to_dg_storage(c->mesh);
+    }
   } catch (const std::bad_alloc&) {
     delete c;
     return NUMA_ENOMEM;
@@ -299,6 +307,7 @@ int numa_get_mesh_info(const numa_ctx* c, numa_mesh_info* info) {
   info->Nl = c->mesh.Nl;
   info->Ng = c->mesh.Ng;
   info->N = c->mesh.N;
+  info->dss_entries = c->mesh.nentries;
   info->workspace_bytes = layout_workspace(c->cfg, c->mesh, nullptr, nullptr);
   return NUMA_OK;
 }
@@ -349,7 +358,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
-  up(L.csr_idx, m.csr_idx.data(), Nl * 4);
+  up(L.csr_idx, m.csr_idx.data(), m.csr_idx.size() * 4);
   up(L.dss_order, m.dss_order.data(), m.dss_order.size());
   up(L.ref, m.ref.data(), 4 * Ng * 8);
   up(L.Minv, m.Minv.data(), Ng * 8);

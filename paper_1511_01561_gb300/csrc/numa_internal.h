@@ -25,7 +25,8 @@ struct HostMesh {
   std::vector<double> gxyz;           // global-node coordinates [3][Ng]
   std::vector<int32_t> l2g;           // element node -> global node [Nl]
   std::vector<int32_t> csr_off;       // global node -> first entry in csr_idx [Ng+1]
-  std::vector<int32_t> csr_idx;       // element nodes of each global node, ascending [Nl]
+  std::vector<int32_t> csr_idx;       // element nodes of each global node, ascending [nentries]
+  long long nentries = 0;             // CSR entries: Nl (CG storage) or sum of the squared counts (DG)
   std::vector<uint8_t> dss_order;     // per block of kDssBlock global nodes: local indices sorted by
                                       // their number of element nodes (stable) [ceil(Ng/kDssBlock)*kDssBlock]
   std::vector<double> met;            // [10][Nl]: dxi_d/dx_c at row 3d+c, then Jw
@@ -38,6 +39,8 @@ struct HostMesh {
 };
 
 bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err);
+// Re-index a built mesh for DG storage (one storage node per element node).
+void expand_to_dg_storage(HostMesh& m);
 bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const double* prm, int nprm,
                      double* q, std::string& err);
 

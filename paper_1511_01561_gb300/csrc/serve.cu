@@ -121,6 +121,7 @@ bool workspace_bytes_of(const numa_config& c, size_t* bytes, long long* Ng) {
     return false;
   }
   m.Nl = m.Ne * m.Np;
+  m.nentries = m.Nl;  // CG storage: one CSR entry per element node
   *bytes = layout_workspace(c, m, nullptr, nullptr);
   *Ng = m.Ng;
   return true;
@@ -327,6 +328,7 @@ int numa_sched_submit(numa_sched* s, const numa_config* cfg, int ic_kind, const 
                       double dt, int nsteps, long long* id) {
   if (!s || !cfg || !id || nparams < 0 || nparams > 8 || (nparams && !params) || nsteps < 0 || !(dt == dt))
     return NUMA_EINVAL;
+  if (cfg->storage != NUMA_STORAGE_CG) return sfail(s, NUMA_EINVAL, "serving takes CG storage only");
   size_t bytes = 0;
   long long Ng = 0;
   if (!workspace_bytes_of(*cfg, &bytes, &Ng)) return sfail(s, NUMA_EINVAL, "bad mesh configuration");

@@ -21,6 +21,7 @@ ERRORS = {-1: "NUMA_EINVAL", -2: "NUMA_ENOMEM", -3: "NUMA_ECUDA", -4: "NUMA_ENON
 MESH = {"box": 0, "shell": 1}
 REF = {"isentropic": 0, "isothermal": 1}
 METRIC_FORM = {"auto": 0, "nodal": 1}
+STORAGE = {"cg": 0, "dg": 1}
 PRECISION = {"fp64": 0, "fp32_mixed": 1, "fp64_pairs": 2}
 IC = {"rest": 0, "bubble": 1, "uniform": 2, "jetwave": 3}
 
@@ -42,13 +43,13 @@ class numa_config(ctypes.Structure):
         ("Rd", ctypes.c_double), ("cp", ctypes.c_double), ("cv", ctypes.c_double),
         ("P00", ctypes.c_double), ("g", ctypes.c_double), ("Omega", ctypes.c_double),
         ("ref_kind", ctypes.c_int), ("theta0", ctypes.c_double), ("T0", ctypes.c_double),
-        ("precision", ctypes.c_int), ("metric_form", ctypes.c_int),
+        ("precision", ctypes.c_int), ("metric_form", ctypes.c_int), ("storage", ctypes.c_int),
     ]
 
 
 class numa_mesh_info(ctypes.Structure):
     _fields_ = [("Ne", ctypes.c_longlong), ("Nl", ctypes.c_longlong), ("Ng", ctypes.c_longlong),
-                ("workspace_bytes", ctypes.c_size_t), ("N", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("N", ctypes.c_int), ("dss_entries", ctypes.c_longlong)]
 
 
 def _load():
@@ -124,6 +125,7 @@ def make_config(cfg: dict, precision: str = "fp64") -> numa_config:
     c.T0 = float(cfg.get("T0", 300.0))
     c.precision = PRECISION[cfg.get("precision", precision)]
     c.metric_form = METRIC_FORM[cfg.get("metric_form", "auto")]
+    c.storage = STORAGE[cfg.get("storage", "cg")]
     return c
 
 
@@ -141,7 +143,8 @@ def numa_create(cfg: dict, precision: str = "fp64") -> ctypes.c_void_p:
 def numa_get_mesh_info(ctx) -> dict:
     info = numa_mesh_info()
     _check(ctx, lib.numa_get_mesh_info(ctx, ctypes.byref(info)))
-    return dict(Ne=info.Ne, Nl=info.Nl, Ng=info.Ng, workspace_bytes=info.workspace_bytes, N=info.N)
+    return dict(Ne=info.Ne, Nl=info.Nl, Ng=info.Ng, workspace_bytes=info.workspace_bytes, N=info.N,
+                dss_entries=info.dss_entries)
 
 
 def numa_bind(ctx, workspace_ptr: int, nbytes: int, stream_ptr: int) -> None:
