@@ -42,6 +42,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-dg", action="store_true", help="skip the DG-storage comparison")
+    p.add_argument("--no-imex", action="store_true", help="skip the 1D-IMEX comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--filter-reps", type=int, default=20, help="filter applications timed (0 skips)")
@@ -479,12 +480,59 @@ def run_mine(args):
                 "volume_ms_avg": vold / nlaunch, "update_ms_avg": 1e3 * upd_s,
                 "update_hbm_frac": update_bytes(Nl, infod["Ng"], fp, 2 / 3, infod["dss_entries"])
                 / upd_s / 1e9 / hbm_gbs}
+    if not args.no_imex:
+        line["imex"] = imex_block(args, numa, torch, dev, barrier, max_ranks)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def imex_block(args, numa, torch, dev, barrier, max_ranks):
+    """The 1D-IMEX leapfrog against SSP-RK3 on the thin box, each at a time
+    step it is stable at: device time per step, node-updates/s (one element
+    kernel per step against three) and model seconds per wall second."""
+    from paper_1511_01561_gb300 import inputs as I
+
+    w = I.WORKLOADS["thin_64x64x8_N4"]
+    out = {"workload": "thin_64x64x8_N4", "unit": UNIT}
+
+    def timed(scheme, dt):
+        s = numa.Solver(w["cfg"], "fp64", device=str(dev))
+        s.set_time_scheme(scheme)
+        s.init_state(*w["ic"])
+        s.run(dt, max(3, args.warmup))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(s.stream)
+        s.run(dt, args.steps)
+        e1.record(s.stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = max_ranks(e0.elapsed_time(e1))
+        vol, upd = s.time_kernels(dt, args.steps)
+        finite = s.check_finite() == 0
+        ng = s.Ng
+        s.close()
+        return ms / args.steps, vol / args.steps, upd / args.steps, finite, ng
+
+    dt_i, dt_e = w["dt"], w["dt_explicit"]
+    ms_i, vol_i, upd_i, fin_i, ng = timed("imex", dt_i)
+    ms_e, vol_e, upd_e, fin_e, _ = timed("ssp3", dt_e)
+    out.update({
+        "global_nodes": ng,
+        "leapfrog_imex": {"dt": dt_i, "ms_per_step": ms_i, "finite": fin_i, "volume_ms": vol_i,
+                          "dss_plus_column_ms": upd_i, "node_updates_per_s": ng / (ms_i * 1e-3),
+                          "model_s_per_s": dt_i / (ms_i * 1e-3)},
+        "ssp_rk3": {"dt": dt_e, "ms_per_step": ms_e, "finite": fin_e, "volume_ms_per_stage": vol_e / STAGES,
+                    "update_ms_per_stage": upd_e / STAGES,
+                    "node_updates_per_s": ng * STAGES / (ms_e * 1e-3), "model_s_per_s": dt_e / (ms_e * 1e-3)},
+    })
+    out["model_time_speedup"] = out["leapfrog_imex"]["model_s_per_s"] / out["ssp_rk3"]["model_s_per_s"]
+    return out
 
 
 def run_serve(args):

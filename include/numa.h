@@ -197,19 +197,43 @@ int numa_rk_step(numa_ctx* ctx, double dt);
  * non-finite value. */
 int numa_run(numa_ctx* ctx, double dt, int nsteps);
 
-/* Explicit time integrators of numa_rk_step / numa_run (Sec. 2.2).
+/* Time integrators of numa_rk_step / numa_run (Sec. 2.2).
  * SSP3: three-stage, third-order strong-stability-preserving RK (Shu-Osher):
  *   q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1));
  *   q_new = 1/3 q + 2/3 (q2 + dt R(q2)).
  * LS54: five-stage, fourth-order low-storage ("2N") RK of Carpenter and
  *   Kennedy: with dq = 0, for i = 1..5: dq <- A_i dq + dt R(q), q <- q + B_i dq.
  *   The paper's integrator has five stages and third order but is not
- *   specified further; this scheme has its stage count and exceeds its order. */
-typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1 } numa_rk_scheme;
+ *   specified further; this scheme has its stage count and exceeds its order.
+ * LEAPFROG_IMEX: the 1D-IMEX scheme of Sec. 2.2 for meshes whose vertical
+ *   resolution is much finer than the horizontal one: an explicit leapfrog
+ *   step, then an implicit correction along each vertical column.  With L the
+ *   linear vertical operator of Eq. 1 about the reference state (for rho',
+ *   the vertical momentum W and Theta': (L q)_rho = -dz W,
+ *   (L q)_W = -dz(c2 Theta') - g rho' (zero at the bottom and top walls),
+ *   (L q)_Theta = -dz(theta0 W), c2 = gamma p0 / Theta0, theta0 = Theta0 / rho0,
+ *   dz the CG derivative along the column), one step is
+ *     q* = qbar^{n-1} + 2 dt R(q^n),
+ *     (I - dt L) q^{n+1} = q* - dt L (2 q^n - qbar^{n-1}),
+ *     qbar^n = q^n + nu (qbar^{n-1} - 2 q^n + q^{n+1})   (Robert-Asselin),
+ *   i.e. the trapezoidal rule over [t^{n-1}, t^{n+1}] for L and leapfrog for
+ *   the rest.  The first step after numa_set_state, numa_init_state,
+ *   numa_bind or a change of scheme starts from q^0 alone:
+ *     (I - dt/2 L) q^1 = q^0 + dt R(q^0) - dt/2 L q^0,  qbar^0 = q^0.
+ *   Each column's system is reduced to a banded system in W and solved with
+ *   LU factors (partial pivoting) made on the host for each new dt.
+ *   Needs a box with walls at the bottom and top, warp 0, FP64 and CG
+ *   storage, and a reference state that depends on z only. */
+typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1, NUMA_LEAPFROG_IMEX = 2 } numa_rk_scheme;
 
 /* Select the integrator (default NUMA_RK_SSP3).  NUMA_EINVAL for another
- * value.  Takes effect at the next step. */
+ * value, or for NUMA_LEAPFROG_IMEX on a configuration it does not support
+ * (numa_last_error says why).  Takes effect at the next step. */
 int numa_set_time_scheme(numa_ctx* ctx, int scheme);
+
+/* Robert-Asselin filter strength nu of NUMA_LEAPFROG_IMEX, 0 <= nu < 0.5
+ * (default 0.05; 0 turns it off).  NUMA_EINVAL outside that range. */
+int numa_set_robert_asselin(numa_ctx* ctx, double nu);
 
 /* Boyd-Vandeven filter (Sec. 2.3), applied as in the time loop of Sec. 6:
  * after every `every`-th step of numa_run / numa_rk_step (the count restarts
@@ -235,11 +259,14 @@ int numa_set_filter(numa_ctx* ctx, int every, int s, double p, double mu);
  * stream).  NUMA_ESTATE before numa_set_filter or numa_bind. */
 int numa_filter(numa_ctx* ctx);
 
-/* Measurement helper: advance the state by nsteps SSP-RK3 steps with plain
- * (non-graph) launches, bracketing every kernel with CUDA events on the
- * bound stream, then wait and return the summed device time in ms of the
- * element volume kernels (*ms_volume) and of the DSS/update kernels
- * (*ms_update), (stages per step) * nsteps launches each. */
+/* Measurement helper: advance the state by nsteps steps of the selected
+ * integrator with plain (non-graph) launches, bracketing every kernel with
+ * CUDA events on the bound stream, then wait and return the summed device
+ * time in ms of the element volume kernels (*ms_volume) and of the
+ * DSS/update kernels (*ms_update), (stages per step) * nsteps launches each.
+ * For NUMA_LEAPFROG_IMEX a step is one stage and *ms_update covers the DSS
+ * launch and the column kernel (a pending start step is the first of the
+ * nsteps). */
 int numa_time_kernels(numa_ctx* ctx, double dt, int nsteps, double* ms_volume, double* ms_update);
 
 /* Non-finite flag raised by any stage update since the last call; resets it.

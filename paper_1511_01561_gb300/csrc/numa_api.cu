@@ -154,7 +154,109 @@ cudaError_t ensure_prim(numa_ctx* c) {
 }
 
 // Stages per step of the context's integrator.
-int rk_stages(const numa_ctx* c) { return c->rk_scheme == NUMA_RK_LS54 ? 5 : 3; }
+int rk_stages(const numa_ctx* c) {
+  return c->rk_scheme == NUMA_RK_LS54 ? 5 : c->rk_scheme == NUMA_LEAPFROG_IMEX ? 1 : 3;
+}
+
+// Device pointers of the 1D-IMEX tables in the workspace: Dz, c2, theta0,
+// then (Lf, Uf) for tau = dt and for tau = dt/2.
+struct ImexPtrs {
+  double *Dz, *c2, *th0, *Lf[2], *Uf[2];
+  int* piv[2];
+};
+
+ImexPtrs imex_ptrs(const numa_ctx* c) {
+  const int nz = c->imex.nz, N = c->imex.N;
+  ImexPtrs p;
+  p.Dz = c->L.imex;
+  p.c2 = p.Dz + (size_t)nz * (2 * N + 1);
+  p.th0 = p.c2 + nz;
+  p.Lf[0] = p.th0 + nz;
+  p.Uf[0] = p.Lf[0] + (size_t)nz * 2 * N;
+  p.Lf[1] = p.Uf[0] + (size_t)nz * (1 + 4 * N);
+  p.Uf[1] = p.Lf[1] + (size_t)nz * 2 * N;
+  p.piv[0] = c->L.imex_piv;
+  p.piv[1] = c->L.imex_piv + nz;
+  return p;
+}
+
+// Host factors of the column matrices for dt and dt/2 into the workspace
+// (when dt changed), with the operator tables; waits for the copies.
+// NUMA_EINVAL when a matrix cannot be factored, NUMA_ECUDA on a CUDA error.
+int imex_prepare(numa_ctx* c, double dt) {
+  cudaError_t e = imex_kernel_setup();
+  if (e != cudaSuccess) return cuda_fail(c, e, "1D-IMEX kernel setup");
+  if (c->imex_factored && c->imex_dt == dt) return NUMA_OK;
+  std::string err;
+  ImexPtrs p = imex_ptrs(c);
+  const ImexTables& t = c->imex;
+  std::vector<double> Lf, Uf;
+  std::vector<int> piv;
+  const size_t nz = (size_t)t.nz;
+  e = cudaMemcpyAsync(p.Dz, t.Dz.data(), t.Dz.size() * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p.c2, t.c2.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p.th0, t.th0.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
+  int ku[2] = {0, 0};
+  for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+    if (!imex_factor(t, f == 0 ? dt : 0.5 * dt, c->cfg.g, Lf, Uf, piv, &ku[f], err)) return fail(c, NUMA_EINVAL, err);
+    e = cudaMemcpyAsync(p.Lf[f], Lf.data(), Lf.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.Uf[f], Uf.data(), Uf.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.piv[f], piv.data(), nz * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors are reused
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "1D-IMEX factor upload");
+  c->imex_ku[0] = ku[0];
+  c->imex_ku[1] = ku[1];
+  c->imex_dt = dt;
+  c->imex_factored = true;
+  return NUMA_OK;
+}
+
+// One 1D-IMEX step on stream s (imex_prepare(dt) done): create_rhs on q^n,
+// DSS + M^-1 into R (the FP64 primitive buffer, free once the element
+// kernel has read it), then the column kernel, which leaves q^{n+1} in q,
+// the filtered q^n in qs and the primitive fields of q^{n+1}.  The start
+// step (no q^{n-1}) uses dt/2 factors, q* = q^0 + dt R and no filter.
+cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  double* R = static_cast<double*>(c->L.prim);
+  cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, c->L.q, c->L.prim, c->L.re), s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess)
+    e = launch_update(c->cfg.precision, update_args(c, c->L.re, c->L.q, c->L.q, R, 0, 0.0, 1.0, 0.0), s);
+  if (e == cudaSuccess) {
+    const ImexPtrs p = imex_ptrs(c);
+    const int f = start ? 1 : 0;
+    ImexArgs a;
+    a.q = c->L.q;
+    a.qs = c->L.qs;
+    a.qprev = start ? c->L.q : c->L.qs;
+    a.R = R;
+    a.Dz = p.Dz;
+    a.c2 = p.c2;
+    a.th0 = p.th0;
+    a.Lf = p.Lf[f];
+    a.Uf = p.Uf[f];
+    a.piv = p.piv[f];
+    a.N = c->imex.N;
+    a.nz = c->imex.nz;
+    a.kl = c->imex.kl;
+    a.ku = c->imex_ku[f];
+    a.cols_per_block = imex_cols_per_block(a.nz);
+    a.ncol = c->imex_ncol;
+    a.Ng = c->mesh.Ng;
+    a.cR = start ? dt : 2.0 * dt;
+    a.tau = start ? 0.5 * dt : dt;
+    a.g = c->cfg.g;
+    a.nu = start ? 0.0 : c->imex_nu;
+    a.flag = c->L.flags;
+    a.pa = prim_args(c, nullptr, c->L.prim);
+    e = launch_imex(a, s);
+  }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+  return e;
+}
 
 // One step of the context's integrator on stream s: per stage create_rhs,
 // then DSS + M^-1 + the stage update, which also leaves the primitive fields
@@ -234,6 +336,11 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.D2 = (float2*)take(PP * 8);
   d.F64 = (double*)take(PP * 8);
   d.F32 = (float*)take(PP * 4);
+  int nz = 0;
+  if (imex_supported(c, nullptr, &nz, nullptr)) {
+    d.imex = (double*)take(imex_table_doubles(nz, c.N) * 8);
+    d.imex_piv = (int*)take(2 * (size_t)nz * sizeof(int));
+  }
   d.bytes = off;
   if (L) *L = d;
   return off;
@@ -379,6 +486,8 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   c->stream = s;
   c->bound = true;
   c->prim_valid = false;
+  c->imex_started = false;
+  c->imex_factored = false;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -407,6 +516,7 @@ int numa_init_state(numa_ctx* c, int kind, const double* params, int nparams) {
   if (!init_state_host(c->cfg, c->mesh, kind, params, nparams, q.data(), c->err)) return NUMA_EINVAL;
   c->prim_valid = false;
   c->filter_count = 0;
+  c->imex_started = false;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q.data(), q.size() * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_init_state upload");
@@ -418,6 +528,7 @@ int numa_set_state(numa_ctx* c, const double* q, int on_device) {
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_set_state before numa_bind");
   c->prim_valid = false;
   c->filter_count = 0;
+  c->imex_started = false;
   cudaError_t e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
@@ -450,7 +561,16 @@ int numa_rk_step(numa_ctx* c, double dt) {
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_rk_step before numa_bind");
   if (!std::isfinite(dt)) return fail(c, NUMA_EINVAL, "dt must be finite");
   cudaError_t e = ensure_prim(c);
-  if (e == cudaSuccess) e = enqueue_rk_step(c, dt, c->stream);
+  if (c->rk_scheme == NUMA_LEAPFROG_IMEX) {
+    if (e == cudaSuccess) {
+      const int rc = imex_prepare(c, dt);
+      if (rc != NUMA_OK) return rc;
+      e = enqueue_imex_step(c, dt, !c->imex_started, c->stream);
+    }
+    if (e == cudaSuccess) c->imex_started = true;
+  } else if (e == cudaSuccess) {
+    e = enqueue_rk_step(c, dt, c->stream);
+  }
   if (e == cudaSuccess && c->filter_every > 0 && ++c->filter_count == c->filter_every) {
     e = enqueue_filter(c, c->stream);
     c->filter_count = 0;
@@ -464,6 +584,11 @@ int numa_run(numa_ctx* c, double dt, int nsteps) {
   if (!c->bound) return fail(c, NUMA_ESTATE, "numa_run before numa_bind");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NUMA_EINVAL, "bad nsteps or dt");
   cudaError_t e = cudaSuccess;
+  const bool imex = c->rk_scheme == NUMA_LEAPFROG_IMEX;
+  if (imex && nsteps > 0) {
+    const int rc = imex_prepare(c, dt);
+    if (rc != NUMA_OK) return rc;
+  }
   if (!c->graph || c->graph_dt != dt || c->graph_q != c->L.q) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
@@ -473,7 +598,7 @@ int numa_run(numa_ctx* c, double dt, int nsteps) {
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t el = enqueue_rk_step(c, dt, c->cap_stream);
+      cudaError_t el = imex ? enqueue_imex_step(c, dt, false, c->cap_stream) : enqueue_rk_step(c, dt, c->cap_stream);
       e = cudaStreamEndCapture(c->cap_stream, &g);
       if (el != cudaSuccess) e = el;
     }
@@ -502,7 +627,12 @@ int numa_run(numa_ctx* c, double dt, int nsteps) {
   }
   if (nsteps > 0) e = ensure_prim(c);
   for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
-    e = cudaGraphLaunch(c->graph, c->stream);
+    if (imex && !c->imex_started) {  // the start step, outside the graph
+      e = enqueue_imex_step(c, dt, true, c->stream);
+      c->imex_started = e == cudaSuccess;
+    } else {
+      e = cudaGraphLaunch(c->graph, c->stream);
+    }
     if (e == cudaSuccess && c->filter_every > 0 && ++c->filter_count == c->filter_every) {
       e = cudaGraphLaunch(c->fgraph, c->stream);
       c->filter_count = 0;
@@ -525,7 +655,22 @@ int numa_time_kernels(numa_ctx* c, double dt, int nsteps, double* ms_volume, dou
   cudaError_t e = ensure_prim(c);
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
-  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = enqueue_rk_step(c, dt, c->stream, &ev[4 * (size_t)ns * t]);
+  if (c->rk_scheme == NUMA_LEAPFROG_IMEX && e == cudaSuccess && nsteps > 0) {
+    const int rc = imex_prepare(c, dt);
+    if (rc != NUMA_OK) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return rc;
+    }
+  }
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
+    if (c->rk_scheme == NUMA_LEAPFROG_IMEX) {
+      e = enqueue_imex_step(c, dt, !c->imex_started, c->stream, &ev[4 * (size_t)t]);
+      if (e == cudaSuccess) c->imex_started = true;
+    } else {
+      e = enqueue_rk_step(c, dt, c->stream, &ev[4 * (size_t)ns * t]);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   double tv = 0.0, tu = 0.0;
   for (size_t t = 0; t < (size_t)ns * nsteps && e == cudaSuccess; ++t) {
@@ -592,12 +737,31 @@ int numa_set_filter(numa_ctx* c, int every, int s, double p, double mu) {
 
 int numa_set_time_scheme(numa_ctx* c, int scheme) {
   if (!c) return NUMA_EINVAL;
-  if (scheme != NUMA_RK_SSP3 && scheme != NUMA_RK_LS54) return fail(c, NUMA_EINVAL, "unknown time scheme");
+  if (scheme != NUMA_RK_SSP3 && scheme != NUMA_RK_LS54 && scheme != NUMA_LEAPFROG_IMEX)
+    return fail(c, NUMA_EINVAL, "unknown time scheme");
+  if (scheme == NUMA_LEAPFROG_IMEX && !c->imex_tables) {
+    std::string why;
+    if (!imex_supported(c->cfg, &c->imex_ncol, nullptr, &why)) return fail(c, NUMA_EINVAL, why);
+    if (!imex_operator(c->cfg, c->mesh, c->imex, why)) return fail(c, NUMA_EINVAL, why);
+    c->imex_tables = true;
+  }
+  if (scheme != c->rk_scheme) c->imex_started = false;
   if (scheme != c->rk_scheme && c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
   c->rk_scheme = scheme;
+  return NUMA_OK;
+}
+
+int numa_set_robert_asselin(numa_ctx* c, double nu) {
+  if (!c) return NUMA_EINVAL;
+  if (!(nu >= 0.0 && nu < 0.5)) return fail(c, NUMA_EINVAL, "Robert-Asselin strength must be in [0, 0.5)");
+  if (nu != c->imex_nu && c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->imex_nu = nu;
   return NUMA_OK;
 }
 

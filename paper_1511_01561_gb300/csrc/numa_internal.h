@@ -77,6 +77,8 @@ struct DevLayout {
   float* D32 = nullptr;      // [P*P]
   double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
+  double* imex = nullptr;    // 1D-IMEX tables (imex_table_doubles), boxes with walled columns only
+  int* imex_piv = nullptr;   // [2][nz] pivots of the two factorisations (dt and dt/2)
   int* flags = nullptr;      // [64]: 0 = non-finite
   size_t bytes = 0;
 };
@@ -143,6 +145,46 @@ struct UpdateArgs {
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
 };
 
+// The column part of one 1D-IMEX leapfrog step (csrc/imex.cu).  Columns of
+// a walled box: column c, level k is global node c + ncol k.  The kernel
+// forms q* = qprev + cR R, applies the implicit vertical correction with the
+// banded LU factors of the Schur matrix, writes q^{n+1} into q, the
+// Robert-Asselin filtered q^n into qs and the primitive fields of q^{n+1}.
+struct ImexArgs {
+  double* q;            // in: q^n, out: q^{n+1} [5][Ng]
+  double* qs;           // out: filtered q^n [5][Ng]
+  const double* qprev;  // filtered q^{n-1}; q itself on the start step
+  const double* R;      // R(q^n) [5][Ng]
+  const double* Dz;     // [nz][2N+1]: column derivative, entry j of row k at column k - N + j
+  const double* c2;     // [nz] gamma p0 / Theta0
+  const double* th0;    // [nz] Theta0 / rho0
+  const double* Lf;     // [nz][kl]: multipliers of elimination step k (rows k+1 .. k+kl)
+  const double* Uf;     // [nz][1 + ku]: 1 / U_kk, then U_{k,k+1} .. U_{k,k+ku}
+  const int* piv;       // [nz]: row swapped with row k at step k
+  int N, nz, kl, ku, cols_per_block;
+  long long ncol, Ng;
+  double cR, tau, g, nu;  // q* = qprev + cR R; (I - tau L) correction; buoyancy; filter strength
+  int* flag;              // non-finite flag
+  PrimArgs pa;            // primitive fields of q^{n+1}
+};
+
+// Host tables of the vertical operator and the factors of one Schur matrix.
+struct ImexTables {
+  int nz = 0, N = 0, kl = 0, ku = 0;
+  std::vector<double> Dz, c2, th0;  // [nz][2N+1], [nz], [nz]
+  std::vector<double> Lf, Uf;       // [nz][kl], [nz][1 + 4N] (ku <= 4N used)
+  std::vector<int> piv;
+};
+
+// 1D-IMEX: whether the configuration has straight walled vertical columns
+// (an unwarped box with walls at the bottom and top, FP64, CG storage), the
+// column count and height, and the host tables (imex_setup.cpp).
+bool imex_supported(const numa_config& c, long long* ncol, int* nz, std::string* why);
+bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::string& err);
+bool imex_factor(const ImexTables& t, double tau, double g, std::vector<double>& Lf, std::vector<double>& Uf,
+                 std::vector<int>& piv, int* ku, std::string& err);
+size_t imex_table_doubles(int nz, int N);
+
 // One application of the Boyd-Vandeven filter (element part).
 struct FilterArgs {
   const double* q;       // state [5][Ng]
@@ -169,6 +211,12 @@ cudaError_t launch_volume_pairs(int N, bool affine, const VolumeArgs& a, cudaStr
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 // the element part of the filter (filter.cu); mode 3 of launch_update does the DSS
 cudaError_t launch_filter(int N, int precision, const FilterArgs& a, cudaStream_t s);
+// Columns per block of the IMEX kernel for columns of nz levels (0: too tall),
+// its shared memory, and its launch (imex.cu).
+int imex_cols_per_block(int nz);
+size_t imex_smem_bytes(int nz, int cols_per_block);
+cudaError_t imex_kernel_setup();
+cudaError_t launch_imex(const ImexArgs& a, cudaStream_t s);
 
 // ---- serving: ragged multi-member launches --------------------------------
 
@@ -226,6 +274,17 @@ struct numa_ctx {
   std::vector<double> filter_F;
   cudaGraphExec_t fgraph = nullptr;
   const double* fgraph_q = nullptr;
+  // 1D-IMEX leapfrog: Robert-Asselin strength, host tables, the dt the
+  // device factors were made for, and whether q^n has a predecessor (false:
+  // the next step is the start step)
+  double imex_nu = 0.05;
+  bool imex_tables = false;
+  numa::ImexTables imex;
+  long long imex_ncol = 0;
+  double imex_dt = 0.0;
+  int imex_ku[2] = {0, 0};  // upper bandwidths of the factors for dt and dt/2
+  bool imex_factored = false;
+  bool imex_started = false;
 };
 
 namespace numa {

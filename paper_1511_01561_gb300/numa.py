@@ -70,6 +70,7 @@ def _load():
         "numa_run": [vp, d, i],
         "numa_set_filter": [vp, i, i, d, d],
         "numa_set_time_scheme": [vp, i],
+        "numa_set_robert_asselin": [vp, d],
         "numa_filter": [vp],
         "numa_check_finite": [vp, ctypes.POINTER(i)],
         "numa_time_kernels": [vp, d, i, dp, dp],
@@ -182,11 +183,15 @@ def numa_run(ctx, dt: float, nsteps: int) -> None:
     _check(ctx, lib.numa_run(ctx, dt, nsteps))
 
 
-RK_SCHEME = {"ssp3": 0, "ls54": 1}
+RK_SCHEME = {"ssp3": 0, "ls54": 1, "imex": 2}
 
 
 def numa_set_time_scheme(ctx, scheme: str) -> None:
     _check(ctx, lib.numa_set_time_scheme(ctx, RK_SCHEME[scheme]))
+
+
+def numa_set_robert_asselin(ctx, nu: float) -> None:
+    _check(ctx, lib.numa_set_robert_asselin(ctx, nu))
 
 
 def numa_set_filter(ctx, every: int, s: int, p: float, mu: float = 1.0) -> None:
@@ -299,9 +304,14 @@ class Solver:
         numa_run(self.ctx, dt, nsteps)
 
     def set_time_scheme(self, scheme: str):
-        """"ssp3" (three-stage SSP-RK3, the default) or "ls54" (five-stage
-        low-storage RK of order four)."""
+        """"ssp3" (three-stage SSP-RK3, the default), "ls54" (five-stage
+        low-storage RK of order four) or "imex" (leapfrog with implicit
+        vertical-column corrections, walled unwarped boxes in FP64)."""
         numa_set_time_scheme(self.ctx, scheme)
+
+    def set_robert_asselin(self, nu: float):
+        """Robert-Asselin filter strength of the "imex" scheme (default 0.05)."""
+        numa_set_robert_asselin(self.ctx, nu)
 
     def set_filter(self, every: int, s: int, p: float, mu: float = 1.0):
         """Boyd-Vandeven filter after every `every`-th step (0: off)."""
