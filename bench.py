@@ -43,6 +43,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-dg", action="store_true", help="skip the DG-storage comparison")
     p.add_argument("--no-imex", action="store_true", help="skip the 1D-IMEX comparison")
+    p.add_argument("--imex-only", action="store_true", help="run only the 1D-IMEX comparison (profiling)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample length")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--filter-reps", type=int, default=20, help="filter applications timed (0 skips)")
@@ -306,6 +307,15 @@ def run_mine(args):
 
     def max_ranks(x: float) -> float:
         return max_over_ranks(dist, x, dev)
+
+    if args.imex_only:
+        # the 1D-IMEX comparison alone (for profiling its kernels)
+        out = imex_block(args, numa, torch, dev, barrier, max_ranks)
+        if rank == 0:
+            print(json.dumps({"imex": out}))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     def measure(precision, form="auto", scheme="ssp3", storage="cg"):
         s = numa.Solver(dict(cfg, metric_form=form, storage=storage), precision, device=str(dev))

@@ -15,9 +15,12 @@
 //   x_W = s_W + y,  x_rho = q*_rho - tau Dz y,  x_Theta = q*_Theta - tau Dz(theta0 y).
 // The Robert-Asselin filter gives qbar^n = q^n + nu (qprev - 2 q^n + x).
 //
-// One block holds cols_per_block consecutive columns in shared memory
-// ([5][nz][cols] doubles); all threads load and store (coalesced along the
-// columns), one thread per column runs the banded solves.
+// One block holds cols_per_block consecutive columns.  Shared memory keeps
+// the two vectors whose neighbours the column derivative reads ([2][nz][cols]
+// doubles); values needed only at their own node (q*_rho, s_W, q*_Theta) go
+// back into R, which the same thread reads at the end.  The derivative
+// applications run over all (level, column) pairs of the block; one thread
+// per column runs the banded LU sweeps.
 #include "kernels_common.cuh"
 
 namespace numa {
@@ -26,62 +29,85 @@ namespace {
 constexpr int kImexThreads = 128;
 constexpr size_t kImexSmemMax = 200 * 1024;
 
+// Band entries [j0, j1] of row k of Dz that can be nonzero: the row of a node
+// inside element e couples to that element's N+1 nodes; a node shared by two
+// elements (k a multiple of N) to both elements' nodes.
+__device__ __forceinline__ void dz_row_range(int k, int N, int nz, int& j0, int& j1) {
+  const int i = k % N;
+  if (i == 0) {
+    j0 = max(0, N - k);
+    j1 = min(2 * N, nz - 1 - k + N);
+  } else {
+    j0 = N - i;  // column k - i, the element's first node
+    j1 = 2 * N - i;
+  }
+}
+
 __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   extern __shared__ __align__(16) double sm[];
-  const int nz = a.nz, CPB = a.cols_per_block, N = a.N, W2 = 2 * a.N + 1;
+  const int nz = a.nz, CPB = a.cols_per_block, N = a.N, W2 = 2 * a.N + 1, kl = a.kl, US = 1 + 4 * a.N;
   const long long Ng = a.Ng, ncol = a.ncol;
   const size_t plane = (size_t)nz * CPB;
-  double* QR = sm;              // q*_rho, then x_rho
-  double* QT = sm + plane;      // q*_Theta, then x_Theta
-  double* SW = sm + 2 * plane;  // s_W, then x_W
-  double* UT = sm + 3 * plane;  // c2 (s_Theta - q*_Theta), then theta0 y
-  double* EY = sm + 4 * plane;  // right-hand side of H y = r, then y
+  double* UT = sm;          // c2 (s_Theta - q*_Theta), then theta0 y
+  double* EY = sm + plane;  // e, then r (right-hand side of H y = r), then y
+  // the factors, read on the serial path of the sweeps, staged once per block
+  double* Ls = EY + plane;                   // [nz][kl]
+  double* Us = Ls + (size_t)nz * kl;         // [nz][1 + 4N]
+  int* Ps = reinterpret_cast<int*>(Us + (size_t)nz * US);  // [nz][3]
+  for (int t = threadIdx.x; t < nz * kl; t += blockDim.x) Ls[t] = a.Lf[t];
+  for (int t = threadIdx.x; t < nz * US; t += blockDim.x) Us[t] = a.Uf[t];
+  for (int t = threadIdx.x; t < 3 * nz; t += blockDim.x) Ps[t] = a.piv[t];
+  double* R = a.R;
   const long long col0 = (long long)blockIdx.x * CPB;
   const double nu = a.nu, tau = a.tau;
+  const int items = nz * CPB;
 
   // explicit step, the filter's first part, U and V finished
-  for (int t = threadIdx.x; t < nz * CPB; t += blockDim.x) {
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
     const int k = t / CPB, cl = t - k * CPB;
     const long long col = col0 + cl;
     if (col >= ncol) continue;
     const long long g = col + ncol * k;
-    double qs_[5], qn_[5];
+    double qst[5], sv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double qn = a.q[v * Ng + g], qp = a.qprev[v * Ng + g];
-      const double qst = fma(a.cR, a.R[v * Ng + g], qp);
-      qs_[v] = qst;
-      qn_[v] = fma(-2.0, qn, qp);  // qprev - 2 q^n
+      qst[v] = fma(a.cR, R[v * Ng + g], qp);
+      sv[v] = fma(2.0, qn, -qp);  // s = 2 q^n - qprev, so qprev - 2 q^n = -s
       if (v == 1 || v == 2) {
-        a.q[v * Ng + g] = qst;
-        a.qs[v * Ng + g] = fma(nu, qn_[v] + qst, qn);
+        a.q[v * Ng + g] = qst[v];
+        a.qs[v * Ng + g] = fma(nu, qst[v] - sv[v], qn);  // x = q* for U and V
       } else {
-        a.qs[v * Ng + g] = fma(nu, qn_[v], qn);  // q^n + nu (qprev - 2 q^n)
+        a.qs[v * Ng + g] = fma(-nu, sv[v], qn);  // q^n + nu (qprev - 2 q^n)
       }
-      qn_[v] = fma(2.0, qn, -qp);  // s = 2 q^n - qprev
     }
+    R[g] = qst[0];
+    R[3 * Ng + g] = sv[3];
+    R[4 * Ng + g] = qst[4];
     const size_t o = (size_t)k * CPB + cl;
-    QR[o] = qs_[0];
-    QT[o] = qs_[4];
-    SW[o] = qn_[3];
-    UT[o] = a.c2[k] * (qn_[4] - qs_[4]);
-    const double e = qs_[3] - qn_[3];
-    EY[o] = (k == 0 || k == nz - 1) ? e : fma(-tau * a.g, qs_[0] - qn_[0], e);
+    UT[o] = a.c2[k] * (sv[4] - qst[4]);
+    const double e = qst[3] - sv[3];
+    EY[o] = (k == 0 || k == nz - 1) ? e : fma(-tau * a.g, qst[0] - sv[0], e);
   }
   __syncthreads();
 
-  const int cl = threadIdx.x;
-  if (cl < CPB && col0 + cl < ncol) {
-    // r = e + tau Dz(c2 (s_Theta - q*_Theta)) on the interior rows
-    for (int k = 1; k < nz - 1; ++k) {
-      const int j0 = max(0, N - k), j1 = min(W2 - 1, nz - 1 - k + N);
-      double acc = 0.0;
-      for (int j = j0; j <= j1; ++j) acc = fma(a.Dz[k * W2 + j], UT[(size_t)(k - N + j) * CPB + cl], acc);
-      EY[(size_t)k * CPB + cl] = fma(tau, acc, EY[(size_t)k * CPB + cl]);
-    }
-    // forward elimination with the recorded row swaps, then back substitution
+  // r = e + tau Dz(c2 (s_Theta - q*_Theta)) on the interior rows
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
+    const int k = t / CPB, cl = t - k * CPB;
+    if (k == 0 || k == nz - 1) continue;
+    int j0, j1;
+    dz_row_range(k, N, nz, j0, j1);
+    double acc = 0.0;
+    for (int j = j0; j <= j1; ++j) acc = fma(a.Dz[k * W2 + j], UT[(size_t)(k - N + j) * CPB + cl], acc);
+    EY[(size_t)k * CPB + cl] = fma(tau, acc, EY[(size_t)k * CPB + cl]);
+  }
+  __syncthreads();
+
+  // H y = r: forward elimination with the recorded row swaps, back substitution
+  for (int cl = threadIdx.x; cl < CPB; cl += blockDim.x) {
+    if (col0 + cl >= ncol) break;
     for (int k = 0; k < nz; ++k) {
-      const int p = a.piv[k];
+      const int p = Ps[3 * k];
       double yk = EY[(size_t)k * CPB + cl];
       if (p != k) {
         const double yp = EY[(size_t)p * CPB + cl];
@@ -89,44 +115,40 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
         EY[(size_t)k * CPB + cl] = yp;
         yk = yp;
       }
-      const int imax = min(a.kl, nz - 1 - k);
+      const int imax = Ps[3 * k + 1];
       for (int i = 1; i <= imax; ++i)
-        EY[(size_t)(k + i) * CPB + cl] = fma(-a.Lf[k * a.kl + i - 1], yk, EY[(size_t)(k + i) * CPB + cl]);
+        EY[(size_t)(k + i) * CPB + cl] = fma(-Ls[k * kl + i - 1], yk, EY[(size_t)(k + i) * CPB + cl]);
     }
-    const int US = 1 + 4 * N;
     for (int k = nz - 1; k >= 0; --k) {
       double acc = EY[(size_t)k * CPB + cl];
-      const int jmax = min(a.ku, nz - 1 - k);
-      for (int j = 1; j <= jmax; ++j) acc = fma(-a.Uf[k * US + j], EY[(size_t)(k + j) * CPB + cl], acc);
-      EY[(size_t)k * CPB + cl] = acc * a.Uf[k * US];
-    }
-    for (int k = 0; k < nz; ++k) UT[(size_t)k * CPB + cl] = a.th0[k] * EY[(size_t)k * CPB + cl];
-    // x_rho = q*_rho - tau Dz y, x_Theta = q*_Theta - tau Dz(theta0 y), x_W = s_W + y
-    for (int k = 0; k < nz; ++k) {
-      const int j0 = max(0, N - k), j1 = min(W2 - 1, nz - 1 - k + N);
-      double dy = 0.0, dty = 0.0;
-      for (int j = j0; j <= j1; ++j) {
-        const double d = a.Dz[k * W2 + j];
-        const size_t o = (size_t)(k - N + j) * CPB + cl;
-        dy = fma(d, EY[o], dy);
-        dty = fma(d, UT[o], dty);
-      }
-      const size_t o = (size_t)k * CPB + cl;
-      QR[o] = fma(-tau, dy, QR[o]);
-      QT[o] = fma(-tau, dty, QT[o]);
-      SW[o] += EY[o];
+      const int jmax = Ps[3 * k + 2];
+      for (int j = 1; j <= jmax; ++j) acc = fma(-Us[k * US + j], EY[(size_t)(k + j) * CPB + cl], acc);
+      EY[(size_t)k * CPB + cl] = acc * Us[k * US];
     }
   }
   __syncthreads();
+  for (int t = threadIdx.x; t < items; t += blockDim.x) UT[t] = a.th0[t / CPB] * EY[t];
+  __syncthreads();
 
+  // x_rho = q*_rho - tau Dz y, x_Theta = q*_Theta - tau Dz(theta0 y), x_W = s_W + y;
   // q^{n+1}, the filtered q^n and the primitive fields of q^{n+1}
-  for (int t = threadIdx.x; t < nz * CPB; t += blockDim.x) {
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
     const int k = t / CPB, c = t - k * CPB;
     const long long col = col0 + c;
     if (col >= ncol) continue;
     const long long g = col + ncol * k;
-    const size_t o = (size_t)k * CPB + c;
-    const double xr = QR[o], xw = SW[o], xt = QT[o];
+    int j0, j1;
+    dz_row_range(k, N, nz, j0, j1);
+    double dy = 0.0, dty = 0.0;
+    for (int j = j0; j <= j1; ++j) {
+      const double d = a.Dz[k * W2 + j];
+      const size_t o = (size_t)(k - N + j) * CPB + c;
+      dy = fma(d, EY[o], dy);
+      dty = fma(d, UT[o], dty);
+    }
+    const double xr = fma(-tau, dy, R[g]);
+    const double xw = R[3 * Ng + g] + EY[(size_t)k * CPB + c];
+    const double xt = fma(-tau, dty, R[4 * Ng + g]);
     a.q[g] = xr;
     a.q[3 * Ng + g] = xw;
     a.q[4 * Ng + g] = xt;
@@ -143,13 +165,23 @@ DeviceFlags imex_attr;
 
 }  // namespace
 
-int imex_cols_per_block(int nz) {
-  for (int c = 32; c >= 1; c /= 2)
-    if (imex_smem_bytes(nz, c) <= kImexSmemMax) return c;
+// Columns per block: kImexColsTarget while a block's shared memory stays
+// under kImexSmemMax / 2, fewer for tall columns.
+constexpr int kImexColsTarget = 32;
+
+int imex_cols_per_block(int nz, int N) {
+  for (int c = kImexColsTarget; c >= 32; c /= 2)
+    if (imex_smem_bytes(nz, N, c) <= kImexSmemMax / 2) return c;
+  for (int c = 16; c >= 1; c /= 2)
+    if (imex_smem_bytes(nz, N, c) <= kImexSmemMax) return c;
   return 0;
 }
 
-size_t imex_smem_bytes(int nz, int cols_per_block) { return 5 * sizeof(double) * (size_t)nz * cols_per_block; }
+// Two column vectors per column, the factors of one Schur matrix (rows of
+// 2N multipliers and 1 + 4N U entries) and the pivot rows.
+size_t imex_smem_bytes(int nz, int N, int cols_per_block) {
+  return sizeof(double) * (size_t)nz * (2 * (size_t)cols_per_block + 2 * N + 1 + 4 * N) + 3 * sizeof(int) * (size_t)nz;
+}
 
 cudaError_t imex_kernel_setup() {
   if (imex_attr.has()) return cudaSuccess;
@@ -163,7 +195,7 @@ cudaError_t launch_imex(const ImexArgs& a, cudaStream_t s) {
   if (a.cols_per_block < 1 || a.cols_per_block > kImexThreads || a.nz < 2 || a.N < 1 || a.kl > 2 * a.N ||
       a.ku > 4 * a.N)
     return cudaErrorInvalidValue;
-  const size_t smem = imex_smem_bytes(a.nz, a.cols_per_block);
+  const size_t smem = imex_smem_bytes(a.nz, a.N, a.cols_per_block);
   if (smem > kImexSmemMax || !imex_attr.has()) return cudaErrorInvalidValue;
   if (a.ncol == 0) return cudaSuccess;
   const long long blocks = (a.ncol + a.cols_per_block - 1) / a.cols_per_block;

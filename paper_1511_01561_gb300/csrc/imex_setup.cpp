@@ -26,7 +26,7 @@ bool imex_supported(const numa_config& c, long long* ncol, int* nz, std::string*
   const long long nx = (long long)c.nex * c.N + (c.periodic[0] ? 0 : 1);
   const long long ny = (long long)c.ney * c.N + (c.periodic[1] ? 0 : 1);
   const long long h = (long long)c.nez * c.N + 1;
-  if (h > 4097 || imex_cols_per_block((int)h) == 0) return no("columns too tall for the column kernel");
+  if (h > 4097 || imex_cols_per_block((int)h, c.N) == 0) return no("columns too tall for the column kernel");
   if (ncol) *ncol = nx * ny;
   if (nz) *nz = (int)h;
   return true;
@@ -110,14 +110,14 @@ bool imex_factor(const ImexTables& t, double tau, double g, std::vector<double>&
   // then the multipliers of step k, in that order
   Lf.assign((size_t)nz * kl, 0.0);
   Uf.assign((size_t)nz * US, 0.0);
-  piv.assign(nz, 0);
+  piv.assign(3 * (size_t)nz, 0);
   int kumax = 0;
   for (int k = 0; k < nz; ++k) {
     const int last = std::min(nz - 1, k + kl);
     int p = k;
     for (int i = k + 1; i <= last; ++i)
       if (std::fabs(H[(size_t)i * nz + k]) > std::fabs(H[(size_t)p * nz + k])) p = i;
-    piv[k] = p;
+    piv[3 * k] = p;
     if (p != k)
       for (int j = k; j < nz; ++j) std::swap(H[(size_t)k * nz + j], H[(size_t)p * nz + j]);
     const double d = H[(size_t)k * nz + k];
@@ -126,17 +126,22 @@ bool imex_factor(const ImexTables& t, double tau, double g, std::vector<double>&
       return false;
     }
     const int jend = std::min(nz - 1, k + 4 * N);
+    int lused = 0, uused = 0;
     for (int i = k + 1; i <= last; ++i) {
       const double f = H[(size_t)i * nz + k] / d;
       Lf[(size_t)k * kl + (i - k - 1)] = f;
       if (f == 0.0) continue;
+      lused = i - k;
       for (int j = k; j <= jend; ++j) H[(size_t)i * nz + j] -= f * H[(size_t)k * nz + j];
     }
     Uf[(size_t)k * US] = 1.0 / d;
     for (int j = 1; j <= 4 * N && k + j < nz; ++j) {
       Uf[(size_t)k * US + j] = H[(size_t)k * nz + k + j];
-      if (H[(size_t)k * nz + k + j] != 0.0) kumax = std::max(kumax, j);
+      if (H[(size_t)k * nz + k + j] != 0.0) uused = j;
     }
+    piv[3 * k + 1] = lused;
+    piv[3 * k + 2] = uused;
+    kumax = std::max(kumax, uused);
     for (int j = k + 4 * N + 1; j < nz; ++j)
       if (H[(size_t)k * nz + j] != 0.0) {
         err = "1D-IMEX: fill outside the band";

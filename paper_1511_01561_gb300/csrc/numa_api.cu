@@ -176,7 +176,7 @@ ImexPtrs imex_ptrs(const numa_ctx* c) {
   p.Lf[1] = p.Uf[0] + (size_t)nz * (1 + 4 * N);
   p.Uf[1] = p.Lf[1] + (size_t)nz * 2 * N;
   p.piv[0] = c->L.imex_piv;
-  p.piv[1] = c->L.imex_piv + nz;
+  p.piv[1] = c->L.imex_piv + 3 * nz;
   return p;
 }
 
@@ -201,7 +201,7 @@ int imex_prepare(numa_ctx* c, double dt) {
     if (!imex_factor(t, f == 0 ? dt : 0.5 * dt, c->cfg.g, Lf, Uf, piv, &ku[f], err)) return fail(c, NUMA_EINVAL, err);
     e = cudaMemcpyAsync(p.Lf[f], Lf.data(), Lf.size() * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.Uf[f], Uf.data(), Uf.size() * 8, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p.piv[f], piv.data(), nz * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.piv[f], piv.data(), 3 * nz * sizeof(int), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors are reused
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "1D-IMEX factor upload");
@@ -243,7 +243,7 @@ cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s
     a.nz = c->imex.nz;
     a.kl = c->imex.kl;
     a.ku = c->imex_ku[f];
-    a.cols_per_block = imex_cols_per_block(a.nz);
+    a.cols_per_block = imex_cols_per_block(a.nz, a.N);
     a.ncol = c->imex_ncol;
     a.Ng = c->mesh.Ng;
     a.cR = start ? dt : 2.0 * dt;
@@ -339,7 +339,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   int nz = 0;
   if (imex_supported(c, nullptr, &nz, nullptr)) {
     d.imex = (double*)take(imex_table_doubles(nz, c.N) * 8);
-    d.imex_piv = (int*)take(2 * (size_t)nz * sizeof(int));
+    d.imex_piv = (int*)take(6 * (size_t)nz * sizeof(int));
   }
   d.bytes = off;
   if (L) *L = d;

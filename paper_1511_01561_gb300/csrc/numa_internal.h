@@ -78,7 +78,7 @@ struct DevLayout {
   double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
   double* imex = nullptr;    // 1D-IMEX tables (imex_table_doubles), boxes with walled columns only
-  int* imex_piv = nullptr;   // [2][nz] pivots of the two factorisations (dt and dt/2)
+  int* imex_piv = nullptr;   // [2][nz][3] pivots and row extents of the two factorisations (dt, dt/2)
   int* flags = nullptr;      // [64]: 0 = non-finite
   size_t bytes = 0;
 };
@@ -154,13 +154,14 @@ struct ImexArgs {
   double* q;            // in: q^n, out: q^{n+1} [5][Ng]
   double* qs;           // out: filtered q^n [5][Ng]
   const double* qprev;  // filtered q^{n-1}; q itself on the start step
-  const double* R;      // R(q^n) [5][Ng]
+  double* R;            // R(q^n) [5][Ng]; overwritten (q*_rho, s_W, q*_Theta kept per node)
   const double* Dz;     // [nz][2N+1]: column derivative, entry j of row k at column k - N + j
   const double* c2;     // [nz] gamma p0 / Theta0
   const double* th0;    // [nz] Theta0 / rho0
   const double* Lf;     // [nz][kl]: multipliers of elimination step k (rows k+1 .. k+kl)
   const double* Uf;     // [nz][1 + ku]: 1 / U_kk, then U_{k,k+1} .. U_{k,k+ku}
-  const int* piv;       // [nz]: row swapped with row k at step k
+  const int* piv;       // [nz][3]: row swapped with row k at step k, multipliers used (last
+                        // nonzero), U entries used (last nonzero) of row k
   int N, nz, kl, ku, cols_per_block;
   long long ncol, Ng;
   double cR, tau, g, nu;  // q* = qprev + cR R; (I - tau L) correction; buoyancy; filter strength
@@ -173,7 +174,7 @@ struct ImexTables {
   int nz = 0, N = 0, kl = 0, ku = 0;
   std::vector<double> Dz, c2, th0;  // [nz][2N+1], [nz], [nz]
   std::vector<double> Lf, Uf;       // [nz][kl], [nz][1 + 4N] (ku <= 4N used)
-  std::vector<int> piv;
+  std::vector<int> piv;             // [nz][3] (see ImexArgs::piv)
 };
 
 // 1D-IMEX: whether the configuration has straight walled vertical columns
@@ -213,8 +214,8 @@ cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_filter(int N, int precision, const FilterArgs& a, cudaStream_t s);
 // Columns per block of the IMEX kernel for columns of nz levels (0: too tall),
 // its shared memory, and its launch (imex.cu).
-int imex_cols_per_block(int nz);
-size_t imex_smem_bytes(int nz, int cols_per_block);
+int imex_cols_per_block(int nz, int N);
+size_t imex_smem_bytes(int nz, int N, int cols_per_block);
 cudaError_t imex_kernel_setup();
 cudaError_t launch_imex(const ImexArgs& a, cudaStream_t s);
 
