@@ -33,7 +33,7 @@ from the definitions below:
   and q^0 itself is left unfiltered.
 
 Meshes: boxes with walls at the bottom and top, without warp (straight
-vertical columns).
+vertical columns), and the cubed-sphere shell (radial columns).
 """
 from __future__ import annotations
 
@@ -96,62 +96,105 @@ def cg_derivative_1d(z: np.ndarray, N: int) -> np.ndarray:
 
 
 class VerticalColumns:
-    """The columns of a walled, unwarped box and the operator L on them."""
+    """The vertical columns of a mesh and the operator L on them.
+
+    Box (unwarped, walls at the bottom and top): the z-lines; W = U_z.
+    Shell: the radial lines; W = U . r_hat with r_hat = x / |x| at each node,
+    and the divergence along the column carries the spherical term:
+        (L q)_rho   = -(dr W + 2 W / r)
+        (L q)_U     = r_hat (-dr(c2 Theta') - g(r) rho')   (zero at the bottom and lid)
+        (L q)_Theta = -(dr(theta0 W) + 2 theta0 W / r)
+    with g(r) = g0 (a / r)^2 and r, dr from the layer construction (uniform
+    layers from r_inner to r_outer, Lobatto points inside each)."""
 
     def __init__(self, mesh: O.Mesh):
         cfg = mesh.cfg
-        assert cfg["kind"] == "box" and not cfg.get("periodic", (0, 0, 0))[2] and cfg.get("warp", 0.0) == 0.0
+        self.shell = cfg["kind"] == "shell"
+        if not self.shell:
+            assert cfg["kind"] == "box" and not cfg.get("periodic", (0, 0, 0))[2] and cfg.get("warp", 0.0) == 0.0
         self.mesh = mesh
-        self.N = int(cfg["N"])
-        self.g = float(cfg["g"])
+        self.N = N = int(cfg["N"])
         gamma = float(cfg["cp"]) / float(cfg["cv"])
         xyz = mesh.coords()
-        # columns: nodes with the same (x, y), ordered by z
+        if self.shell:
+            rad = np.sqrt((xyz ** 2).sum(axis=0))
+            dirs = np.round(xyz / rad, 9)
+            keyv, height = [tuple(d) for d in dirs.T], rad
+        else:
+            keyv, height = list(zip(xyz[0], xyz[1])), xyz[2]
         keys = {}
-        for n, (x, y) in enumerate(zip(xyz[0], xyz[1])):
-            keys.setdefault((x, y), []).append(n)
-        cols = [sorted(v, key=lambda n: xyz[2, n]) for v in keys.values()]
+        for n, key in enumerate(keyv):
+            keys.setdefault(key, []).append(n)
+        cols = [sorted(v, key=lambda n: height[n]) for v in keys.values()]
         nz = len(cols[0])
         assert all(len(c) == nz for c in cols)
         self.cols = np.array(cols, dtype=np.int64)  # [ncol][nz] global nodes
         self.nz = nz
         rho0, Th0, p0 = mesh.ref()
-        self.Dz = [cg_derivative_1d(xyz[2, c], self.N) for c in self.cols]
         self.c2 = gamma * p0 / Th0
         self.theta0 = Th0 / rho0
-        # W rows vanish at the bottom and top walls (wall bit 2: normal to z)
-        self.zwall = (mesh.wall() & 4) != 0
+        if self.shell:
+            a, nl = float(cfg["r_inner"]), int(cfg["nlayer"])
+            dR = (float(cfg["r_outer"]) - a) / nl
+            xi, _ = O.lgl(N)
+            h = np.array([(e + 0.5 * (xi[k] + 1.0)) * dR for e in range(nl) for k in range(N)] + [nl * dR])
+            r = a + h
+            self.Dz = [cg_derivative_1d(h, N)] * len(self.cols)
+            self.glev = float(cfg["g"]) * (a / r) ** 2
+            self.r2 = 2.0 / r
+            self.nhat = xyz / rad
+            self.zwall = (mesh.wall() & 8) != 0
+        else:
+            self.Dz = [cg_derivative_1d(xyz[2, c], N) for c in self.cols]
+            self.glev = np.full(nz, float(cfg["g"]))
+            self.r2 = np.zeros(nz)
+            self.nhat = np.zeros_like(xyz)
+            self.nhat[2] = 1.0
+            # W rows vanish at the bottom and top walls (wall bit 2: normal to z)
+            self.zwall = (mesh.wall() & 4) != 0
+
+    def radial(self, q: np.ndarray) -> np.ndarray:
+        """W = U . r_hat at every node."""
+        return (q[1:4] * self.nhat).sum(axis=0)
 
     def apply(self, q: np.ndarray) -> np.ndarray:
         """L q for a state q [5][Ng]."""
         out = np.zeros_like(q)
+        Wall = self.radial(q)
         for c, Dz in zip(self.cols, self.Dz):
-            rho, W, Th = q[0, c], q[3, c], q[4, c]
-            out[0, c] = -Dz @ W
-            out[3, c] = np.where(self.zwall[c], 0.0, -Dz @ (self.c2[c] * Th) - self.g * rho)
-            out[4, c] = -Dz @ (self.theta0[c] * W)
+            rho, W, Th = q[0, c], Wall[c], q[4, c]
+            out[0, c] = -(Dz @ W + self.r2 * W)
+            LW = np.where(self.zwall[c], 0.0, -Dz @ (self.c2[c] * Th) - self.glev * rho)
+            out[1:4, c] = self.nhat[:, c] * LW
+            tw = self.theta0[c] * W
+            out[4, c] = -(Dz @ tw + self.r2 * tw)
         return out
 
     def block(self, c: int) -> np.ndarray:
         """L on column c as a dense [3 nz][3 nz] matrix over (rho', W, Theta')."""
         nodes, Dz, nz = self.cols[c], self.Dz[c], self.nz
+        G = Dz + np.diag(self.r2)  # the divergence along the column
         keep = np.where(self.zwall[nodes], 0.0, 1.0)[:, None]
         Lc = np.zeros((3 * nz, 3 * nz))
-        Lc[:nz, nz:2 * nz] = -Dz
-        Lc[nz:2 * nz, :nz] = -self.g * np.eye(nz) * keep
+        Lc[:nz, nz:2 * nz] = -G
+        Lc[nz:2 * nz, :nz] = -np.diag(self.glev) * keep
         Lc[nz:2 * nz, 2 * nz:] = -(Dz * self.c2[nodes][None, :]) * keep
-        Lc[2 * nz:, nz:2 * nz] = -Dz * self.theta0[nodes][None, :]
+        Lc[2 * nz:, nz:2 * nz] = -G * self.theta0[nodes][None, :]
         return Lc
 
     def solve(self, tau: float, b: np.ndarray) -> np.ndarray:
-        """x with (I - tau L) x = b: a dense solve per column; U, V pass through."""
+        """x with (I - tau L) x = b: a dense solve per column for (rho', W,
+        Theta'); the momentum keeps the part of b_U across the column,
+        x_U = b_U + (x_W - b_U . r_hat) r_hat."""
         x = b.copy()
         nz = self.nz
+        bW = self.radial(b)
         for c in range(len(self.cols)):
             nodes = self.cols[c]
-            rhs = np.concatenate([b[0, nodes], b[3, nodes], b[4, nodes]])
+            rhs = np.concatenate([b[0, nodes], bW[nodes], b[4, nodes]])
             sol = np.linalg.solve(np.eye(3 * nz) - tau * self.block(c), rhs)
-            x[0, nodes], x[3, nodes], x[4, nodes] = sol[:nz], sol[nz:2 * nz], sol[2 * nz:]
+            x[0, nodes], x[4, nodes] = sol[:nz], sol[2 * nz:]
+            x[1:4, nodes] = b[1:4, nodes] + (sol[nz:2 * nz] - bW[nodes]) * self.nhat[:, nodes]
         return x
 
 

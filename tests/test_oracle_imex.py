@@ -169,3 +169,61 @@ def test_imex_stable_past_the_explicit_limit(orc, imex):
     ref = m.run(q0, 0.02, int(round(T / 0.02)))
     assert np.abs(qi[3] - ref[3]).max() <= 0.1 * np.abs(ref[3]).max()
     assert np.abs(qi[0] - ref[0]).max() <= 0.05 * np.abs(ref[0]).max()
+
+
+def _thin_shell(N, lid=12e3, npanel=2, nlayer=3):
+    cfg = I.shell(npanel, nlayer, N)
+    cfg["r_outer"] = cfg["r_inner"] + lid
+    return cfg
+
+
+def test_L_is_the_linearised_rhs_on_the_shell(orc, imex):
+    """Radial perturbations W(r) r_hat, rho'(r), Theta'(r) on the cubed-sphere
+    shell: the rho', radial-momentum and Theta' tendencies of the linearised
+    full RHS are L's, spherical divergence term 2 W / r included; the
+    horizontal momentum tendency, which L leaves to the explicit part, is a
+    discretisation error that falls with N."""
+    horiz = []
+    for N in (3, 5):
+        cfg = _thin_shell(N)
+        m = orc.Mesh(cfg)
+        cols = imex.VerticalColumns(m)
+        xyz = m.coords()
+        h = (np.sqrt((xyz**2).sum(0)) - cfg["r_inner"]) / 12e3
+        rho0, Th0, _ = m.ref()
+        W = rho0 * np.sin(np.pi * h) * np.cos(1.3 * h)
+        W[(m.wall() & 8) != 0] = 0.0
+        dq = np.zeros((5, m.Ng))
+        dq[0] = 1e-3 * rho0 * np.sin(2.1 * h + 0.3)
+        dq[1:4] = cols.nhat * W
+        dq[4] = 1e-3 * Th0 * np.cos(3.0 * h)
+        Lq = cols.apply(dq)
+        eps = 1e-3
+        fd = (m.rhs(eps * dq) - m.rhs(-eps * dq)) / (2 * eps)
+        fW, LW = cols.radial(fd), cols.radial(Lq)
+        for a, b in ((fd[0], Lq[0]), (fW, LW), (fd[4], Lq[4])):
+            assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+        # without the 2 W / r term the density tendency is off at the 1e-4 level
+        G_only = -np.concatenate([Dz @ W[c] for c, Dz in zip(cols.cols, cols.Dz)])
+        idx = np.concatenate(list(cols.cols))
+        assert np.abs(G_only - fd[0][idx]).max() > 1e-5 * np.abs(Lq[0]).max()
+        horiz.append(np.abs(fd[1:4] - fW * cols.nhat).max() / np.abs(LW).max())
+    assert horiz[0] < 0.05 and horiz[1] < 0.7 * horiz[0], horiz
+
+
+def test_imex_on_the_shell_second_order_and_stable(orc, imex):
+    cfg = _thin_shell(4)
+    m = orc.Mesh(cfg)
+    cols = imex.VerticalColumns(m)
+    q0 = m.init_state("jetwave", I.JETWAVE_PARAMS)
+    T = 4.0
+    res = [imex.run_imex(m, q0, dt, int(round(T / dt)), 0.0, cols)[0] for dt in (0.2, 0.1, 0.05)]
+    d1, d2 = res[0] - res[1], res[1] - res[2]
+    ratios = [np.abs(d1[v]).max() / np.abs(d2[v]).max() for v in range(5)]
+    assert all(3.3 < r < 4.8 for r in ratios), ratios
+    # dt = 20 s: vertical acoustic Courant number near 10; SSP-RK3 already fails at 3 s
+    qr = m.run(q0, 3.0, 100)
+    assert not (np.isfinite(qr).all() and np.abs(qr).max() < 1e6)
+    ref = m.run(q0, 0.5, 600)
+    qi, _ = imex.run_imex(m, q0, 20.0, 15, 0.05, cols)
+    assert np.abs(qi[1:4] - ref[1:4]).max() <= 0.01 * np.abs(ref[1:4]).max()
