@@ -501,47 +501,50 @@ def run_mine(args):
 
 
 def imex_block(args, numa, torch, dev, barrier, max_ranks):
-    """The 1D-IMEX leapfrog against SSP-RK3 on the thin box, each at a time
-    step it is stable at: device time per step, node-updates/s (one element
-    kernel per step against three) and model seconds per wall second."""
+    """The 1D-IMEX leapfrog against SSP-RK3 on the thin box (z-columns) and
+    the cubed-sphere shell (radial columns), each scheme at a time step it is
+    stable at: device time per step, node-updates/s (one element kernel per
+    step against three) and model seconds per wall second."""
     from paper_1511_01561_gb300 import inputs as I
 
-    w = I.WORKLOADS["thin_64x64x8_N4"]
-    out = {"workload": "thin_64x64x8_N4", "unit": UNIT}
+    out = {"unit": UNIT, "workloads": {}}
+    for name in ("thin_64x64x8_N4", "shell_6x30x30x8_N4"):
+        w = I.WORKLOADS[name]
 
-    def timed(scheme, dt):
-        s = numa.Solver(w["cfg"], "fp64", device=str(dev))
-        s.set_time_scheme(scheme)
-        s.init_state(*w["ic"])
-        s.run(dt, max(3, args.warmup))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0.record(s.stream)
-        s.run(dt, args.steps)
-        e1.record(s.stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-        ms = max_ranks(e0.elapsed_time(e1))
-        vol, upd = s.time_kernels(dt, args.steps)
-        finite = s.check_finite() == 0
-        ng = s.Ng
-        s.close()
-        return ms / args.steps, vol / args.steps, upd / args.steps, finite, ng
+        def timed(scheme, dt):
+            s = numa.Solver(w["cfg"], "fp64", device=str(dev))
+            s.set_time_scheme(scheme)
+            s.init_state(*w["ic"])
+            s.run(dt, max(3, args.warmup))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            torch.cuda.synchronize(dev)
+            e0.record(s.stream)
+            s.run(dt, args.steps)
+            e1.record(s.stream)
+            torch.cuda.synchronize(dev)
+            barrier()
+            ms = max_ranks(e0.elapsed_time(e1))
+            vol, upd = s.time_kernels(dt, args.steps)
+            finite = s.check_finite() == 0
+            ng = s.Ng
+            s.close()
+            return ms / args.steps, vol / args.steps, upd / args.steps, finite, ng
 
-    dt_i, dt_e = w["dt"], w["dt_explicit"]
-    ms_i, vol_i, upd_i, fin_i, ng = timed("imex", dt_i)
-    ms_e, vol_e, upd_e, fin_e, _ = timed("ssp3", dt_e)
-    out.update({
-        "global_nodes": ng,
-        "leapfrog_imex": {"dt": dt_i, "ms_per_step": ms_i, "finite": fin_i, "volume_ms": vol_i,
-                          "dss_plus_column_ms": upd_i, "node_updates_per_s": ng / (ms_i * 1e-3),
-                          "model_s_per_s": dt_i / (ms_i * 1e-3)},
-        "ssp_rk3": {"dt": dt_e, "ms_per_step": ms_e, "finite": fin_e, "volume_ms_per_stage": vol_e / STAGES,
-                    "update_ms_per_stage": upd_e / STAGES,
-                    "node_updates_per_s": ng * STAGES / (ms_e * 1e-3), "model_s_per_s": dt_e / (ms_e * 1e-3)},
-    })
-    out["model_time_speedup"] = out["leapfrog_imex"]["model_s_per_s"] / out["ssp_rk3"]["model_s_per_s"]
+        dt_i, dt_e = w["dt_imex"], w["dt_explicit"]
+        ms_i, vol_i, upd_i, fin_i, ng = timed("imex", dt_i)
+        ms_e, vol_e, upd_e, fin_e, _ = timed("ssp3", dt_e)
+        r = {
+            "global_nodes": ng,
+            "leapfrog_imex": {"dt": dt_i, "ms_per_step": ms_i, "finite": fin_i, "volume_ms": vol_i,
+                              "dss_plus_column_ms": upd_i, "node_updates_per_s": ng / (ms_i * 1e-3),
+                              "model_s_per_s": dt_i / (ms_i * 1e-3)},
+            "ssp_rk3": {"dt": dt_e, "ms_per_step": ms_e, "finite": fin_e, "volume_ms_per_stage": vol_e / STAGES,
+                        "update_ms_per_stage": upd_e / STAGES,
+                        "node_updates_per_s": ng * STAGES / (ms_e * 1e-3), "model_s_per_s": dt_e / (ms_e * 1e-3)},
+        }
+        r["model_time_speedup"] = r["leapfrog_imex"]["model_s_per_s"] / r["ssp_rk3"]["model_s_per_s"]
+        out["workloads"][name] = r
     return out
 
 

@@ -1,18 +1,20 @@
 // Column part of the 1D-IMEX leapfrog step (Sec. 2.2: an explicit leapfrog
 // step, then implicit corrections along each vertical column of grid points;
-// the IMEX line of the time loop in Sec. 6).
+// the IMEX line of the time loop in Sec. 6), for the z-columns of a box and
+// the radial columns of the cubed-sphere shell.
 //
 // With the explicit tendency R = R(q^n) already in memory, per column:
 //   q*  = qprev + cR R                      (cR = 2 dt; dt on the start step)
 //   s   = 2 q^n - qprev                     (q^0 on the start step)
 //   solve (I - tau L) x = q* - tau L s for rho', W, Theta'; U, V take q*.
-// L couples rho', W and Theta' through the column derivative Dz; eliminating
-// rho' and Theta' leaves the Schur system H x_W = f in W,
-//   H = I - tau^2 (Dz C2 Dz T0 + g Dz)      (identity rows at the walls),
+// L couples rho', W (the momentum along the column) and Theta' through the
+// column derivative Dz and the divergence G = Dz + 2/r (G = Dz in the box);
+// eliminating rho' and Theta' leaves the Schur system H x_W = f in W,
+//   H = I - tau^2 (Dz C2 G T0 + g G)        (identity rows at the walls),
 // which in the increment y = x_W - s reads
 //   H y = q*_W - s_W - tau g (q*_rho - s_rho) + tau Dz(c2 (s_Theta - q*_Theta))
 // (q*_W - s_W at the walls), after which
-//   x_W = s_W + y,  x_rho = q*_rho - tau Dz y,  x_Theta = q*_Theta - tau Dz(theta0 y).
+//   x_W = s_W + y,  x_rho = q*_rho - tau G y,  x_Theta = q*_Theta - tau G(theta0 y).
 // The Robert-Asselin filter gives qbar^n = q^n + nu (qprev - 2 q^n + x).
 //
 // One block holds cols_per_block consecutive columns.  Shared memory keeps
@@ -43,6 +45,10 @@ __device__ __forceinline__ void dz_row_range(int k, int N, int nz, int& j0, int&
   }
 }
 
+// RADIAL = false: z-columns of the box (node c + ncol k, W = U_z);
+// RADIAL = true: radial columns of the shell (node cols[c nz + k],
+// W = U . r_hat, U^{n+1} = U* + (x_W - W*) r_hat).
+template <bool RADIAL>
 __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int nz = a.nz, CPB = a.cols_per_block, N = a.N, W2 = 2 * a.N + 1, kl = a.kl, US = 1 + 4 * a.N;
@@ -61,33 +67,46 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   const long long col0 = (long long)blockIdx.x * CPB;
   const double nu = a.nu, tau = a.tau;
   const int items = nz * CPB;
+  auto node = [&](long long col, int k) -> long long {
+    if constexpr (RADIAL) return a.cols[col * nz + k];
+    else return col + ncol * k;
+  };
 
-  // explicit step, the filter's first part, U and V finished
+  // explicit step, the filter's first part; U and V finished in the box,
+  // U* parked in q on the shell
   for (int t = threadIdx.x; t < items; t += blockDim.x) {
     const int k = t / CPB, cl = t - k * CPB;
     const long long col = col0 + cl;
     if (col >= ncol) continue;
-    const long long g = col + ncol * k;
+    const long long g = node(col, k);
     double qst[5], sv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double qn = a.q[v * Ng + g], qp = a.qprev[v * Ng + g];
       qst[v] = fma(a.cR, R[v * Ng + g], qp);
       sv[v] = fma(2.0, qn, -qp);  // s = 2 q^n - qprev, so qprev - 2 q^n = -s
-      if (v == 1 || v == 2) {
+      if (!RADIAL && (v == 1 || v == 2)) {
         a.q[v * Ng + g] = qst[v];
         a.qs[v * Ng + g] = fma(nu, qst[v] - sv[v], qn);  // x = q* for U and V
       } else {
+        if (RADIAL && v >= 1 && v <= 3) a.q[v * Ng + g] = qst[v];
         a.qs[v * Ng + g] = fma(-nu, sv[v], qn);  // q^n + nu (qprev - 2 q^n)
       }
     }
+    double wst = qst[3], swv = sv[3];
+    if constexpr (RADIAL) {
+      const double nx = a.nrm[g], ny = a.nrm[Ng + g], nz_ = a.nrm[2 * Ng + g];
+      wst = fma(qst[1], nx, fma(qst[2], ny, qst[3] * nz_));
+      swv = fma(sv[1], nx, fma(sv[2], ny, sv[3] * nz_));
+      R[Ng + g] = wst;
+    }
     R[g] = qst[0];
-    R[3 * Ng + g] = sv[3];
+    R[3 * Ng + g] = swv;
     R[4 * Ng + g] = qst[4];
     const size_t o = (size_t)k * CPB + cl;
     UT[o] = a.c2[k] * (sv[4] - qst[4]);
-    const double e = qst[3] - sv[3];
-    EY[o] = (k == 0 || k == nz - 1) ? e : fma(-tau * a.g, qst[0] - sv[0], e);
+    const double e = wst - swv;
+    EY[o] = (k == 0 || k == nz - 1) ? e : fma(-tau * a.gl[k], qst[0] - sv[0], e);
   }
   __syncthreads();
 
@@ -130,13 +149,13 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   for (int t = threadIdx.x; t < items; t += blockDim.x) UT[t] = a.th0[t / CPB] * EY[t];
   __syncthreads();
 
-  // x_rho = q*_rho - tau Dz y, x_Theta = q*_Theta - tau Dz(theta0 y), x_W = s_W + y;
-  // q^{n+1}, the filtered q^n and the primitive fields of q^{n+1}
+  // x_rho = q*_rho - tau G y, x_Theta = q*_Theta - tau G(theta0 y), x_W = s_W + y
+  // (G = Dz + 2/r); q^{n+1}, the filtered q^n and the primitive fields of q^{n+1}
   for (int t = threadIdx.x; t < items; t += blockDim.x) {
     const int k = t / CPB, c = t - k * CPB;
     const long long col = col0 + c;
     if (col >= ncol) continue;
-    const long long g = col + ncol * k;
+    const long long g = node(col, k);
     int j0, j1;
     dz_row_range(k, N, nz, j0, j1);
     double dy = 0.0, dty = 0.0;
@@ -146,22 +165,48 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
       dy = fma(d, EY[o], dy);
       dty = fma(d, UT[o], dty);
     }
+    const size_t o = (size_t)k * CPB + c;
+    const double yk = EY[o];
+    if constexpr (RADIAL) {
+      dy = fma(a.r2[k], yk, dy);
+      dty = fma(a.r2[k], UT[o], dty);
+    }
     const double xr = fma(-tau, dy, R[g]);
-    const double xw = R[3 * Ng + g] + EY[(size_t)k * CPB + c];
+    const double xw = R[3 * Ng + g] + yk;
     const double xt = fma(-tau, dty, R[4 * Ng + g]);
     a.q[g] = xr;
-    a.q[3 * Ng + g] = xw;
     a.q[4 * Ng + g] = xt;
     a.qs[g] = fma(nu, xr, a.qs[g]);
-    a.qs[3 * Ng + g] = fma(nu, xw, a.qs[3 * Ng + g]);
     a.qs[4 * Ng + g] = fma(nu, xt, a.qs[4 * Ng + g]);
-    const double xu = a.q[Ng + g], xv = a.q[2 * Ng + g];
-    if (nonfinite(xr) | nonfinite(xu) | nonfinite(xv) | nonfinite(xw) | nonfinite(xt)) atomicOr(a.flag, 1);
-    write_prim(a.pa, g, xr, xu, xv, xw, xt);
+    double xu, xv, xz;
+    if constexpr (RADIAL) {
+      const double dw = xw - R[Ng + g];  // x_W - W*
+      xu = fma(dw, a.nrm[g], a.q[Ng + g]);
+      xv = fma(dw, a.nrm[Ng + g], a.q[2 * Ng + g]);
+      xz = fma(dw, a.nrm[2 * Ng + g], a.q[3 * Ng + g]);
+      a.q[Ng + g] = xu;
+      a.q[2 * Ng + g] = xv;
+      a.qs[Ng + g] = fma(nu, xu, a.qs[Ng + g]);
+      a.qs[2 * Ng + g] = fma(nu, xv, a.qs[2 * Ng + g]);
+    } else {
+      xu = a.q[Ng + g];
+      xv = a.q[2 * Ng + g];
+      xz = xw;
+    }
+    a.q[3 * Ng + g] = xz;
+    a.qs[3 * Ng + g] = fma(nu, xz, a.qs[3 * Ng + g]);
+    if (nonfinite(xr) | nonfinite(xu) | nonfinite(xv) | nonfinite(xz) | nonfinite(xt)) atomicOr(a.flag, 1);
+    write_prim(a.pa, g, xr, xu, xv, xz, xt);
   }
 }
 
 DeviceFlags imex_attr;
+
+template <bool RADIAL>
+cudaError_t set_imex_attr() {
+  return cudaFuncSetAttribute(imex_column_kernel<RADIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kImexSmemMax);
+}
 
 }  // namespace
 
@@ -185,8 +230,8 @@ size_t imex_smem_bytes(int nz, int N, int cols_per_block) {
 
 cudaError_t imex_kernel_setup() {
   if (imex_attr.has()) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(imex_column_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImexSmemMax);
+  cudaError_t e = set_imex_attr<false>();
+  if (e == cudaSuccess) e = set_imex_attr<true>();
   if (e == cudaSuccess) imex_attr.set();
   return e;
 }
@@ -199,7 +244,9 @@ cudaError_t launch_imex(const ImexArgs& a, cudaStream_t s) {
   if (smem > kImexSmemMax || !imex_attr.has()) return cudaErrorInvalidValue;
   if (a.ncol == 0) return cudaSuccess;
   const long long blocks = (a.ncol + a.cols_per_block - 1) / a.cols_per_block;
-  imex_column_kernel<<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
+  if ((a.cols != nullptr) != (a.nrm != nullptr)) return cudaErrorInvalidValue;
+  if (a.cols) imex_column_kernel<true><<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
+  else imex_column_kernel<false><<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

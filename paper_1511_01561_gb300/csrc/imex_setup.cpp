@@ -1,7 +1,8 @@
 // Host tables of the 1D-IMEX column correction (Sec. 2.2): the CG
 // derivative along a vertical column, the linearisation coefficients of the
 // reference state, and the banded LU factors (partial pivoting) of the Schur
-// matrix H = I - tau^2 (Dz C2 Dz T0 + g Dz) that the column kernel solves.
+// matrix H = I - tau^2 (Dz C2 G T0 + g G) that the column kernel solves, with
+// G = Dz + 2/r the divergence along the column (G = Dz in the box).
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -17,25 +18,87 @@ bool imex_supported(const numa_config& c, long long* ncol, int* nz, std::string*
     if (why) *why = w;
     return false;
   };
-  if (c.mesh_kind != NUMA_MESH_BOX) return no("1D-IMEX needs a box mesh (vertical columns along z)");
-  if (c.periodic[2]) return no("1D-IMEX needs walls at the bottom and top (not periodic in z)");
-  if (c.warp != 0.0) return no("1D-IMEX needs straight columns (warp = 0)");
   if (c.precision != NUMA_FP64) return no("1D-IMEX runs in FP64");
   if (c.storage != NUMA_STORAGE_CG) return no("1D-IMEX runs with CG storage");
-  if (c.N < 1 || c.nex < 1 || c.ney < 1 || c.nez < 1) return no("bad mesh");
-  const long long nx = (long long)c.nex * c.N + (c.periodic[0] ? 0 : 1);
-  const long long ny = (long long)c.ney * c.N + (c.periodic[1] ? 0 : 1);
-  const long long h = (long long)c.nez * c.N + 1;
+  long long cols = 0, h = 0;
+  if (c.mesh_kind == NUMA_MESH_BOX) {
+    if (c.periodic[2]) return no("1D-IMEX needs walls at the bottom and top (not periodic in z)");
+    if (c.warp != 0.0) return no("1D-IMEX needs straight columns (warp = 0)");
+    if (c.N < 1 || c.nex < 1 || c.ney < 1 || c.nez < 1) return no("bad mesh");
+    cols = ((long long)c.nex * c.N + (c.periodic[0] ? 0 : 1)) * ((long long)c.ney * c.N + (c.periodic[1] ? 0 : 1));
+    h = (long long)c.nez * c.N + 1;
+  } else if (c.mesh_kind == NUMA_MESH_SHELL) {
+    if (c.N < 1 || c.npanel < 1 || c.nlayer < 1) return no("bad mesh");
+    const long long K = (long long)c.npanel * c.N;
+    cols = 6 * K * K + 2;
+    h = (long long)c.nlayer * c.N + 1;
+  } else {
+    return no("unknown mesh kind");
+  }
   if (h > 4097 || imex_cols_per_block((int)h, c.N) == 0) return no("columns too tall for the column kernel");
-  if (ncol) *ncol = nx * ny;
+  if (ncol) *ncol = cols;
   if (nz) *nz = (int)h;
   return true;
 }
 
 size_t imex_table_doubles(int nz, int N) {
   const size_t n = (size_t)nz;
-  return n * (2 * N + 1) + 2 * n + 2 * (n * 2 * N + n * (1 + 4 * N));
+  return n * (2 * N + 1) + 4 * n + 2 * (n * 2 * N + n * (1 + 4 * N));
 }
+
+namespace {
+
+// Radial columns of the shell: walk the element columns (layers are the
+// fastest element index) and record, per surface point, its global node at
+// every level.
+bool shell_columns(const numa_config& c, const HostMesh& m, long long ncol, int nz, std::vector<int32_t>& cols,
+                   std::string& err) {
+  const int N = m.N, P = m.P, nl = c.nlayer;
+  const long long ecols = m.Ne / nl;
+  cols.assign((size_t)ncol * nz, -1);
+  std::vector<int32_t> col_of((size_t)m.Ng, -1);
+  long long next = 0;
+  for (long long ec = 0; ec < ecols; ++ec)
+    for (int j = 0; j < P; ++j)
+      for (int i = 0; i < P; ++i) {
+        const int32_t bottom = m.l2g[(ec * nl) * m.Np + i + P * j];
+        int32_t col = col_of[bottom];
+        const bool fresh = col < 0;
+        if (fresh) {
+          if (next >= ncol) {
+            err = "1D-IMEX: more radial columns than surface points";
+            return false;
+          }
+          col = (int32_t)next++;
+          col_of[bottom] = col;
+        }
+        for (int il = 0; il < nl; ++il)
+          for (int k = (il == 0 ? 0 : 1); k < P; ++k) {
+            const int32_t g = m.l2g[(ec * nl + il) * m.Np + i + P * (j + P * k)];
+            int32_t& slot = cols[(size_t)col * nz + il * N + k];
+            if (fresh) slot = g;
+            else if (slot != g) {
+              err = "1D-IMEX: inconsistent radial column";
+              return false;
+            }
+          }
+      }
+  if (next != ncol) {
+    err = "1D-IMEX: radial columns do not cover the surface";
+    return false;
+  }
+  std::vector<char> seen((size_t)m.Ng, 0);
+  for (int32_t g : cols) {
+    if (g < 0 || g >= m.Ng || seen[g]) {
+      err = "1D-IMEX: radial columns do not partition the nodes";
+      return false;
+    }
+    seen[g] = 1;
+  }
+  return true;
+}
+
+}  // namespace
 
 bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::string& err) {
   long long ncol = 0;
@@ -47,21 +110,37 @@ bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::
     err = "1D-IMEX: unexpected node count";
     return false;
   }
-  // the reference state must be the same in every column (it depends on z only)
+  const bool shell = c.mesh_kind == NUMA_MESH_SHELL;
+  t.cols.clear();
+  if (shell && !shell_columns(c, m, ncol, nz, t.cols, err)) return false;
+  auto node = [&](long long col, int k) -> long long {
+    return shell ? t.cols[(size_t)col * nz + k] : col + (long long)k * ncol;
+  };
+  // the reference state must be the same in every column (it depends on the height only)
   for (int v = 0; v < 3; ++v)
     for (int k = 0; k < nz; ++k) {
-      const double r = m.ref[v * Ng + (long long)k * ncol];
+      const double r = m.ref[v * Ng + node(0, k)];
       for (long long col = 1; col < ncol; ++col)
-        if (m.ref[v * Ng + col + (long long)k * ncol] != r) {
+        if (m.ref[v * Ng + node(col, k)] != r) {
           err = "1D-IMEX: the reference state varies along a level";
           return false;
         }
     }
+  // heights of the levels: box z; shell the layer construction, uniform
+  // layers with Lobatto points inside each
   std::vector<double> z(nz);
-  for (int k = 0; k < nz; ++k) z[k] = m.gxyz[2 * Ng + (long long)k * ncol];
+  const int nez = shell ? c.nlayer : c.nez;
+  if (shell) {
+    const double dR = (c.r_outer - c.r_inner) / c.nlayer;
+    for (int il = 0; il < c.nlayer; ++il)
+      for (int k = 0; k < N; ++k) z[il * N + k] = (il + 0.5 * (1.0 + m.xi[k])) * dR;
+    z[nz - 1] = c.nlayer * dR;
+  } else {
+    for (int k = 0; k < nz; ++k) z[k] = m.gxyz[2 * Ng + node(0, k)];
+  }
   // A_KM = sum_e w_k D_km (the Jacobian dz/2 cancels against dxi/dz), mass_K = sum_e w_k dz_e / 2
   std::vector<double> A((size_t)nz * W2, 0.0), mass(nz, 0.0);
-  for (int e = 0; e < c.nez; ++e) {
+  for (int e = 0; e < nez; ++e) {
     const double h = z[(e + 1) * N] - z[e * N];
     for (int k = 0; k < P; ++k) {
       const int K = e * N + k;
@@ -78,30 +157,42 @@ bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::
   const double gamma = c.cp / c.cv;
   t.c2.resize(nz);
   t.th0.resize(nz);
+  t.gl.resize(nz);
+  t.r2.resize(nz);
   for (int k = 0; k < nz; ++k) {
-    const long long g = (long long)k * ncol;
+    const long long g = node(0, k);
     t.c2[k] = gamma * m.ref[2 * Ng + g] / m.ref[Ng + g];
     t.th0[k] = m.ref[Ng + g] / m.ref[g];
+    if (shell) {
+      const double r = c.r_inner + z[k];
+      t.gl[k] = c.g * (c.r_inner / r) * (c.r_inner / r);
+      t.r2[k] = 2.0 / r;
+    } else {
+      t.gl[k] = c.g;
+      t.r2[k] = 0.0;
+    }
   }
   return true;
 }
 
-bool imex_factor(const ImexTables& t, double tau, double g, std::vector<double>& Lf, std::vector<double>& Uf,
+bool imex_factor(const ImexTables& t, double tau, std::vector<double>& Lf, std::vector<double>& Uf,
                  std::vector<int>& piv, int* ku, std::string& err) {
   const int nz = t.nz, N = t.N, W2 = 2 * N + 1, kl = 2 * N, US = 1 + 4 * N;
   auto dz = [&](int i, int j) -> double {
     const int d = j - i + N;
     return (d >= 0 && d < W2) ? t.Dz[(size_t)i * W2 + d] : 0.0;
   };
-  // H = I - tau^2 (Dz C2 Dz T0 + g Dz) on the interior rows, identity rows at the walls
+  // G = Dz + diag(2/r): the divergence along the column
+  auto gd = [&](int i, int j) -> double { return i == j ? dz(i, j) + t.r2[i] : dz(i, j); };
+  // H = I - tau^2 (Dz C2 G T0 + g G) on the interior rows, identity rows at the walls
   std::vector<double> H((size_t)nz * nz, 0.0);
   for (int i = 0; i < nz; ++i) {
     H[(size_t)i * nz + i] = 1.0;
     if (i == 0 || i == nz - 1) continue;
     for (int j = std::max(0, i - kl); j <= std::min(nz - 1, i + kl); ++j) {
       double s = 0.0;
-      for (int l = std::max(0, i - N); l <= std::min(nz - 1, i + N); ++l) s += dz(i, l) * t.c2[l] * dz(l, j);
-      s = s * t.th0[j] + g * dz(i, j);
+      for (int l = std::max(0, i - N); l <= std::min(nz - 1, i + N); ++l) s += dz(i, l) * t.c2[l] * gd(l, j);
+      s = s * t.th0[j] + t.gl[i] * gd(i, j);
       H[(size_t)i * nz + j] -= tau * tau * s;
     }
   }

@@ -159,9 +159,9 @@ int rk_stages(const numa_ctx* c) {
 }
 
 // Device pointers of the 1D-IMEX tables in the workspace: Dz, c2, theta0,
-// then (Lf, Uf) for tau = dt and for tau = dt/2.
+// g(r), 2/r, then (Lf, Uf) for tau = dt and for tau = dt/2.
 struct ImexPtrs {
-  double *Dz, *c2, *th0, *Lf[2], *Uf[2];
+  double *Dz, *c2, *th0, *gl, *r2, *Lf[2], *Uf[2];
   int* piv[2];
 };
 
@@ -171,7 +171,9 @@ ImexPtrs imex_ptrs(const numa_ctx* c) {
   p.Dz = c->L.imex;
   p.c2 = p.Dz + (size_t)nz * (2 * N + 1);
   p.th0 = p.c2 + nz;
-  p.Lf[0] = p.th0 + nz;
+  p.gl = p.th0 + nz;
+  p.r2 = p.gl + nz;
+  p.Lf[0] = p.r2 + nz;
   p.Uf[0] = p.Lf[0] + (size_t)nz * 2 * N;
   p.Lf[1] = p.Uf[0] + (size_t)nz * (1 + 4 * N);
   p.Uf[1] = p.Lf[1] + (size_t)nz * 2 * N;
@@ -196,9 +198,14 @@ int imex_prepare(numa_ctx* c, double dt) {
   e = cudaMemcpyAsync(p.Dz, t.Dz.data(), t.Dz.size() * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.c2, t.c2.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.th0, t.th0.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p.gl, t.gl.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p.r2, t.r2.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !t.cols.empty())
+    e = cudaMemcpyAsync(c->L.imex_cols, t.cols.data(), t.cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        c->stream);
   int ku[2] = {0, 0};
   for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
-    if (!imex_factor(t, f == 0 ? dt : 0.5 * dt, c->cfg.g, Lf, Uf, piv, &ku[f], err)) return fail(c, NUMA_EINVAL, err);
+    if (!imex_factor(t, f == 0 ? dt : 0.5 * dt, Lf, Uf, piv, &ku[f], err)) return fail(c, NUMA_EINVAL, err);
     e = cudaMemcpyAsync(p.Lf[f], Lf.data(), Lf.size() * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.Uf[f], Uf.data(), Uf.size() * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.piv[f], piv.data(), 3 * nz * sizeof(int), cudaMemcpyHostToDevice, c->stream);
@@ -236,6 +243,11 @@ cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s
     a.Dz = p.Dz;
     a.c2 = p.c2;
     a.th0 = p.th0;
+    a.gl = p.gl;
+    a.r2 = p.r2;
+    const bool shell = c->cfg.mesh_kind == NUMA_MESH_SHELL;
+    a.cols = shell ? c->L.imex_cols : nullptr;
+    a.nrm = shell ? c->L.nrm : nullptr;
     a.Lf = p.Lf[f];
     a.Uf = p.Uf[f];
     a.piv = p.piv[f];
@@ -248,7 +260,6 @@ cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s
     a.Ng = c->mesh.Ng;
     a.cR = start ? dt : 2.0 * dt;
     a.tau = start ? 0.5 * dt : dt;
-    a.g = c->cfg.g;
     a.nu = start ? 0.0 : c->imex_nu;
     a.flag = c->L.flags;
     a.pa = prim_args(c, nullptr, c->L.prim);
@@ -337,9 +348,11 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.F64 = (double*)take(PP * 8);
   d.F32 = (float*)take(PP * 4);
   int nz = 0;
-  if (imex_supported(c, nullptr, &nz, nullptr)) {
+  long long ncol = 0;
+  if (imex_supported(c, &ncol, &nz, nullptr)) {
     d.imex = (double*)take(imex_table_doubles(nz, c.N) * 8);
     d.imex_piv = (int*)take(6 * (size_t)nz * sizeof(int));
+    if (c.mesh_kind == NUMA_MESH_SHELL) d.imex_cols = (int32_t*)take((size_t)ncol * nz * sizeof(int32_t));
   }
   d.bytes = off;
   if (L) *L = d;

@@ -79,6 +79,7 @@ struct DevLayout {
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
   double* imex = nullptr;    // 1D-IMEX tables (imex_table_doubles), boxes with walled columns only
   int* imex_piv = nullptr;   // [2][nz][3] pivots and row extents of the two factorisations (dt, dt/2)
+  int32_t* imex_cols = nullptr;  // shell: [ncol][nz] global nodes of the radial columns
   int* flags = nullptr;      // [64]: 0 = non-finite
   size_t bytes = 0;
 };
@@ -146,7 +147,8 @@ struct UpdateArgs {
 };
 
 // The column part of one 1D-IMEX leapfrog step (csrc/imex.cu).  Columns of
-// a walled box: column c, level k is global node c + ncol k.  The kernel
+// a walled box: column c, level k is global node c + ncol k; radial columns
+// of the shell: global node cols[c nz + k], W = U . r_hat.  The kernel
 // forms q* = qprev + cR R, applies the implicit vertical correction with the
 // banded LU factors of the Schur matrix, writes q^{n+1} into q, the
 // Robert-Asselin filtered q^n into qs and the primitive fields of q^{n+1}.
@@ -158,13 +160,17 @@ struct ImexArgs {
   const double* Dz;     // [nz][2N+1]: column derivative, entry j of row k at column k - N + j
   const double* c2;     // [nz] gamma p0 / Theta0
   const double* th0;    // [nz] Theta0 / rho0
+  const double* gl;     // [nz] gravity g(r) at each level (the box: g)
+  const double* r2;     // [nz] 2 / r at each level, the spherical divergence term (the box: 0)
+  const int32_t* cols;  // shell: [ncol][nz] global nodes of each radial column; box: null
+  const double* nrm;    // shell: r_hat [3][Ng]; box: null
   const double* Lf;     // [nz][kl]: multipliers of elimination step k (rows k+1 .. k+kl)
   const double* Uf;     // [nz][1 + ku]: 1 / U_kk, then U_{k,k+1} .. U_{k,k+ku}
   const int* piv;       // [nz][3]: row swapped with row k at step k, multipliers used (last
                         // nonzero), U entries used (last nonzero) of row k
   int N, nz, kl, ku, cols_per_block;
   long long ncol, Ng;
-  double cR, tau, g, nu;  // q* = qprev + cR R; (I - tau L) correction; buoyancy; filter strength
+  double cR, tau, nu;     // q* = qprev + cR R; (I - tau L) correction; filter strength
   int* flag;              // non-finite flag
   PrimArgs pa;            // primitive fields of q^{n+1}
 };
@@ -173,6 +179,8 @@ struct ImexArgs {
 struct ImexTables {
   int nz = 0, N = 0, kl = 0, ku = 0;
   std::vector<double> Dz, c2, th0;  // [nz][2N+1], [nz], [nz]
+  std::vector<double> gl, r2;       // [nz] g(r) and 2 / r per level (box: g and 0)
+  std::vector<int32_t> cols;        // shell: [ncol][nz] global nodes of the radial columns
   std::vector<double> Lf, Uf;       // [nz][kl], [nz][1 + 4N] (ku <= 4N used)
   std::vector<int> piv;             // [nz][3] (see ImexArgs::piv)
 };
@@ -182,7 +190,7 @@ struct ImexTables {
 // column count and height, and the host tables (imex_setup.cpp).
 bool imex_supported(const numa_config& c, long long* ncol, int* nz, std::string* why);
 bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::string& err);
-bool imex_factor(const ImexTables& t, double tau, double g, std::vector<double>& Lf, std::vector<double>& Uf,
+bool imex_factor(const ImexTables& t, double tau, std::vector<double>& Lf, std::vector<double>& Uf,
                  std::vector<int>& piv, int* ku, std::string& err);
 size_t imex_table_doubles(int nz, int N);
 
