@@ -222,8 +222,13 @@ int numa_run(numa_ctx* ctx, double dt, int nsteps);
  *     (I - dt/2 L) q^1 = q^0 + dt R(q^0) - dt/2 L q^0,  qbar^0 = q^0.
  *   Each column's system is reduced to a banded system in W and solved with
  *   LU factors (partial pivoting) made on the host for each new dt.
- *   Needs a box with walls at the bottom and top, warp 0, FP64 and CG
- *   storage, and a reference state that depends on z only. */
+ *   Columns: the z-lines of a box with walls at the bottom and top and warp
+ *   0, or the radial lines of the cubed-sphere shell, where W = U . r_hat,
+ *   dz is the radial derivative, the divergence terms are
+ *   (L q)_rho = -(dr W + 2 W / r) and (L q)_Theta = -(dr(theta0 W) + 2 theta0 W / r),
+ *   g = g0 (a / r)^2, and the correction moves U along r_hat only.
+ *   Needs FP64, CG storage and a reference state that depends on the height
+ *   only. */
 typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1, NUMA_LEAPFROG_IMEX = 2 } numa_rk_scheme;
 
 /* Select the integrator (default NUMA_RK_SSP3).  NUMA_EINVAL for another
