@@ -227,8 +227,8 @@ int numa_run(numa_ctx* ctx, double dt, int nsteps);
  *   dz is the radial derivative, the divergence terms are
  *   (L q)_rho = -(dr W + 2 W / r) and (L q)_Theta = -(dr(theta0 W) + 2 theta0 W / r),
  *   g = g0 (a / r)^2, and the correction moves U along r_hat only.
- *   Needs FP64, CG storage and a reference state that depends on the height
- *   only. */
+ *   Needs FP64 or FP64-pairs precision, CG storage and a reference state
+ *   that depends on the height only. */
 typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1, NUMA_LEAPFROG_IMEX = 2 } numa_rk_scheme;
 
 /* Select the integrator (default NUMA_RK_SSP3).  NUMA_EINVAL for another

@@ -18,7 +18,8 @@ bool imex_supported(const numa_config& c, long long* ncol, int* nz, std::string*
     if (why) *why = w;
     return false;
   };
-  if (c.precision != NUMA_FP64) return no("1D-IMEX runs in FP64");
+  // R is parked in the primitive buffer: 40 B per node, which the FP32 form's 32 B do not hold
+  if (c.precision != NUMA_FP64 && c.precision != NUMA_FP64_PAIRS) return no("1D-IMEX runs in FP64 or FP64-pairs");
   if (c.storage != NUMA_STORAGE_CG) return no("1D-IMEX runs with CG storage");
   long long cols = 0, h = 0;
   if (c.mesh_kind == NUMA_MESH_BOX) {

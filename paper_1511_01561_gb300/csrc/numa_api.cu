@@ -220,8 +220,9 @@ int imex_prepare(numa_ctx* c, double dt) {
 }
 
 // One 1D-IMEX step on stream s (imex_prepare(dt) done): create_rhs on q^n,
-// DSS + M^-1 into R (the FP64 primitive buffer, free once the element
-// kernel has read it), then the column kernel, which leaves q^{n+1} in q,
+// DSS + M^-1 into R (the primitive buffer, 40 B per node in FP64 and 64 B in
+// the pairs mode, free once the element kernel has read it; R[v][g] lies
+// inside node g's own primitive slots), then the column kernel, which leaves q^{n+1} in q,
 // the filtered q^n in qs and the primitive fields of q^{n+1}.  The start
 // step (no q^{n-1}) uses dt/2 factors, q* = q^0 + dt R and no filter.
 cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s, cudaEvent_t* ev = nullptr) {

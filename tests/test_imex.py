@@ -40,15 +40,15 @@ def _thin_shell(N, lid=12e3, npanel=2, nlayer=3):
 def test_imex_accepts_walled_unwarped_fp64_boxes_and_shells(lib):
     for cfg in (THIN, I.box((2, 2, 3), 4, periodic=(1, 1, 0)), I.box(1, 1), I.shell(2, 1, 3), _thin_shell(4)):
         assert _scheme_rc(lib, cfg)[0] == 0
+        assert _scheme_rc(lib, cfg, "fp64_pairs")[0] == 0
 
 
 @pytest.mark.parametrize("cfg,precision,word", [
     (I.box(2, 3, periodic=(0, 0, 1)), "fp64", "bottom and top"),
     (I.box(2, 3, warp=0.05), "fp64", "warp"),
     (I.box(2, 3), "fp32_mixed", "FP64"),
-    (I.box(2, 3), "fp64_pairs", "FP64"),
     (dict(I.box(2, 3), storage="dg"), "fp64", "CG storage"),
-], ids=["periodic_z", "warped", "fp32", "pairs", "dg"])
+], ids=["periodic_z", "warped", "fp32", "dg"])
 def test_imex_refuses(lib, cfg, precision, word):
     rc, msg = _scheme_rc(lib, cfg, precision)
     assert rc == -1 and word in msg
@@ -113,8 +113,8 @@ SHELL_CASES = [
 ]
 
 
-def _gpu_run(numa, cfg, ic, dt, nsteps, nu, single=False):
-    sv = numa.Solver(cfg, "fp64")
+def _gpu_run(numa, cfg, ic, dt, nsteps, nu, single=False, precision="fp64"):
+    sv = numa.Solver(cfg, precision)
     try:
         sv.set_time_scheme("imex")
         sv.set_robert_asselin(nu)
@@ -145,9 +145,24 @@ def test_imex_parity(numa, orc, name, cfg, ic, dt, nsteps, nu):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("name,cfg,ic,dt", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_imex_parity_pairs(numa, orc, name, cfg, ic, dt):
+    """The pairs mode's element kernel (FP64-level error) under the same scheme."""
+    from oracle import imex
+
+    m = orc.Mesh(cfg)
+    q0 = m.init_state(*ic)
+    ref, _ = imex.run_imex(m, q0, dt, 12, 0.1)
+    got = _gpu_run(numa, cfg, ic, dt, 12, 0.1, precision="fp64_pairs")
+    err = rel_errors(got, ref, state_floors(ref, m.ref()[0].max()))
+    assert err.max() <= 1e-10, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp64_pairs"])
 @pytest.mark.parametrize("nsteps,nu", [(1, 0.1), (2, 0.1), (10, 0.1), (10, 0.0)])
 @pytest.mark.parametrize("name,cfg,dt", SHELL_CASES, ids=[c[0] for c in SHELL_CASES])
-def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu):
+def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu, precision):
     """Radial columns of the cubed-sphere shell, past the explicit limit; the
     oracle's node order differs, so states are matched by coordinates."""
     from oracle import imex
@@ -158,7 +173,7 @@ def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu):
     ic = ("jetwave", I.JETWAVE_PARAMS)
     q0 = m.init_state(*ic)
     ref, _ = imex.run_imex(m, q0, dt, nsteps, nu)
-    sv = numa.Solver(cfg, "fp64")
+    sv = numa.Solver(cfg, precision)
     try:
         perm = match_nodes(sv.coords(), m.coords(), tol=1e-3)
         sv.set_time_scheme("imex")
