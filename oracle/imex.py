@@ -202,3 +202,24 @@ def run_imex(mesh: O.Mesh, q0: np.ndarray, dt: float, nsteps: int, nu: float, co
     """The 1D-IMEX leapfrog on a box mesh: (q^nsteps, filtered q^{nsteps-1})."""
     cols = cols or VerticalColumns(mesh)
     return lf_imex_run(mesh.rhs, cols.apply, cols.solve, np.ascontiguousarray(q0, dtype=np.float64), dt, nsteps, nu)
+
+
+def run_imex_filtered(mesh: O.Mesh, q0: np.ndarray, dt: float, nsteps: int, nu: float, every: int, s: int,
+                      p: float, mu: float, cols: VerticalColumns = None):
+    """The 1D-IMEX leapfrog with the Boyd-Vandeven filter after every
+    `every`-th step, as the time loop of Sec. 6 orders them: the IMEX
+    correction (and the Robert-Asselin average, which takes the unfiltered
+    q^{n+1}), then the filter of q^{n+1} with DSS and M^-1.  Returns
+    (q^nsteps, filtered q^{nsteps-1})."""
+    cols = cols or VerticalColumns(mesh)
+    R, Lop, solve = mesh.rhs, cols.apply, cols.solve
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    if nsteps == 0:
+        return q0.copy(), q0.copy()
+    prev, cur = q0.copy(), lf_imex_start(R, Lop, solve, q0, dt)
+    for n in range(1, nsteps + 1):
+        if n > 1:
+            cur, prev = lf_imex_step(R, Lop, solve, prev, cur, dt, nu)
+        if every > 0 and n % every == 0:
+            cur = mesh.filter(cur, s, p, mu)
+    return cur, prev

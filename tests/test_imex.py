@@ -189,6 +189,32 @@ def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu, precision):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp64_pairs"])
+def test_imex_with_the_filter(numa, orc, precision):
+    """The Boyd-Vandeven filter after every second step, after the IMEX
+    correction as in the time loop of Sec. 6."""
+    from oracle import imex
+
+    cfg, ic, dt = THIN, ("bubble", THIN_BUBBLE), 0.4
+    m = orc.Mesh(cfg)
+    q0 = m.init_state(*ic)
+    ref, _ = imex.run_imex_filtered(m, q0, dt, 9, 0.1, 2, 2, 12.0, 0.5)
+    assert not np.allclose(ref, imex.run_imex(m, q0, dt, 9, 0.1)[0], rtol=0, atol=1e-9)
+    sv = numa.Solver(cfg, precision)
+    try:
+        sv.set_time_scheme("imex")
+        sv.set_robert_asselin(0.1)
+        sv.set_filter(2, 2, 12.0, 0.5)
+        sv.init_state(*ic)
+        sv.run(dt, 9)
+        got = sv.get_state().numpy().copy()
+    finally:
+        sv.close()
+    err = rel_errors(got, ref, state_floors(ref, m.ref()[0].max()))
+    assert err.max() <= 1e-10, err
+
+
+@pytest.mark.gpu
 def test_imex_graph_equals_single_steps_and_restarts(numa):
     cfg, ic, dt = THIN, ("bubble", THIN_BUBBLE), 0.4
     a = _gpu_run(numa, cfg, ic, dt, 9, 0.1)

@@ -227,3 +227,18 @@ def test_imex_on_the_shell_second_order_and_stable(orc, imex):
     ref = m.run(q0, 0.5, 600)
     qi, _ = imex.run_imex(m, q0, 20.0, 15, 0.05, cols)
     assert np.abs(qi[1:4] - ref[1:4]).max() <= 0.01 * np.abs(ref[1:4]).max()
+
+
+def test_filtered_imex_run_composes(orc, imex):
+    """The filtered run is the plain run when the filter never fires, and
+    when it is the identity (mu = 0: DSS(Jw q) / M = q for a continuous q)
+    it matches to rounding; a real filter changes the state."""
+    m = orc.Mesh(THIN)
+    q0 = m.init_state("bubble", THIN_BUBBLE)
+    plain, plain_prev = imex.run_imex(m, q0, 0.4, 7, 0.1)
+    never, never_prev = imex.run_imex_filtered(m, q0, 0.4, 7, 0.1, 0, 2, 12.0, 0.5)
+    assert np.array_equal(plain, never) and np.array_equal(plain_prev, never_prev)
+    ident, _ = imex.run_imex_filtered(m, q0, 0.4, 7, 0.1, 1, 2, 12.0, 0.0)
+    assert np.abs(ident - plain).max() <= 1e-12 * np.abs(plain).max()
+    filt, _ = imex.run_imex_filtered(m, q0, 0.4, 7, 0.1, 2, 2, 12.0, 0.5)
+    assert np.abs(filt - plain).max() > 1e-6 * np.abs(plain).max()
