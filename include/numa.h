@@ -188,7 +188,9 @@ int numa_rhs_static_scratch(numa_ctx* ctx, const double* q_dev, double* r_dev);
 /* Advance the context's state by one step of size dt of the selected
  * integrator (numa_set_time_scheme; SSP-RK3 by default; Sec. 2.2 explicit
  * stages: per stage create_rhs, DSS with the inverse mass matrix, update q).
- * Enqueued on the bound stream; returns without waiting. */
+ * Enqueued on the bound stream; returns without waiting, except that the
+ * first NUMA_LEAPFROG_IMEX step with a new dt factors the column matrices on
+ * the host and waits for their upload. */
 int numa_rk_step(numa_ctx* ctx, double dt);
 
 /* nsteps steps of the selected integrator (one captured CUDA graph per step,
