@@ -246,3 +246,34 @@ def test_imex_time_kernels(numa):
         assert sv.check_finite() == 0
     finally:
         sv.close()
+
+
+@pytest.mark.gpu
+def test_imex_tall_columns(numa, orc):
+    """145 levels per column: fewer columns per CTA (16), so half a warp runs
+    the banded sweeps; still the oracle's result."""
+    from oracle import imex
+
+    cfg = I.box((2, 2, 36), 4, L=(2000.0, 2000.0, 3600.0))
+    ic = ("bubble", (0.5, 900.0, 1000.0, 1000.0, 1500.0))
+    m = orc.Mesh(cfg)
+    ref, _ = imex.run_imex(m, m.init_state(*ic), 0.05, 3, 0.1)
+    got = _gpu_run(numa, cfg, ic, 0.05, 3, 0.1)
+    err = rel_errors(got, ref, state_floors(ref, m.ref()[0].max()))
+    assert err.max() <= 1e-10, err
+
+
+@pytest.mark.gpu
+def test_imex_reports_a_non_finite_state(numa):
+    sv = numa.Solver(THIN, "fp64")
+    try:
+        sv.set_time_scheme("imex")
+        sv.init_state("bubble", THIN_BUBBLE)
+        q = sv.get_state().numpy().copy()
+        q[4, 17] = np.nan
+        sv.set_state(q)
+        with pytest.raises(numa.NumaError) as e:
+            sv.run(0.4, 2)
+        assert e.value.code == -4
+    finally:
+        sv.close()
