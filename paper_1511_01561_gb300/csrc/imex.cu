@@ -46,7 +46,7 @@ __device__ __forceinline__ void dz_row_range(int k, int N, int nz, int& j0, int&
 }
 
 // RADIAL = false: z-columns of the box (node c + ncol k, W = U_z);
-// RADIAL = true: radial columns of the shell (node cols[c nz + k],
+// RADIAL = true: radial columns of the shell (node cols[k ncol + c],
 // W = U . r_hat, U^{n+1} = U* + (x_W - W*) r_hat).
 template <bool RADIAL>
 __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   const double nu = a.nu, tau = a.tau;
   const int items = nz * CPB;
   auto node = [&](long long col, int k) -> long long {
-    if constexpr (RADIAL) return a.cols[col * nz + k];
+    if constexpr (RADIAL) return a.cols[col + ncol * k];
     else return col + ncol * k;
   };
 

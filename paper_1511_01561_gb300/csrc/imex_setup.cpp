@@ -51,7 +51,8 @@ namespace {
 
 // Radial columns of the shell: walk the element columns (layers are the
 // fastest element index) and record, per surface point, its global node at
-// every level.
+// every level; stored [level][column], so that a warp reading one level of
+// consecutive columns reads consecutive entries.
 bool shell_columns(const numa_config& c, const HostMesh& m, long long ncol, int nz, std::vector<int32_t>& cols,
                    std::string& err) {
   const int N = m.N, P = m.P, nl = c.nlayer;
@@ -76,7 +77,7 @@ bool shell_columns(const numa_config& c, const HostMesh& m, long long ncol, int 
         for (int il = 0; il < nl; ++il)
           for (int k = (il == 0 ? 0 : 1); k < P; ++k) {
             const int32_t g = m.l2g[(ec * nl + il) * m.Np + i + P * (j + P * k)];
-            int32_t& slot = cols[(size_t)col * nz + il * N + k];
+            int32_t& slot = cols[(size_t)(il * N + k) * ncol + col];
             if (fresh) slot = g;
             else if (slot != g) {
               err = "1D-IMEX: inconsistent radial column";
@@ -115,7 +116,7 @@ bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::
   t.cols.clear();
   if (shell && !shell_columns(c, m, ncol, nz, t.cols, err)) return false;
   auto node = [&](long long col, int k) -> long long {
-    return shell ? t.cols[(size_t)col * nz + k] : col + (long long)k * ncol;
+    return shell ? t.cols[(size_t)k * ncol + col] : col + (long long)k * ncol;
   };
   // the reference state must be the same in every column (it depends on the height only)
   for (int v = 0; v < 3; ++v)
