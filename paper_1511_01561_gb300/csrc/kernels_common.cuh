@@ -177,17 +177,12 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     // u and theta are FP32 fields, so rho and Theta are summed in FP32; p'
     // (the reference-state subtraction of the equation of state) in FP64, to
     // the accuracy of the float it is stored as
-    float* w = static_cast<float*>(a.prim);
+    // node-interleaved: two float4 per node, one 32-byte sector
+    float4* w = static_cast<float4*>(a.prim);
     const float rf = 1.0f / (d2f(rho0) + d2f(rp));
     const float Uxf = d2f(Ux), Uyf = d2f(Uy), Uzf = d2f(Uz);
-    w[I] = Uxf;
-    w[Ng + I] = Uyf;
-    w[2 * Ng + I] = Uzf;
-    w[3 * Ng + I] = Uxf * rf;
-    w[4 * Ng + I] = Uyf * rf;
-    w[5 * Ng + I] = Uzf * rf;
-    w[6 * Ng + I] = (d2f(Th0) + d2f(Tp)) * rf;
-    w[7 * Ng + I] = d2f(p0 * eos_ratio<true>(Tp * iTh0, a));
+    w[2 * I] = make_float4(Uxf, Uyf, Uzf, Uxf * rf);
+    w[2 * I + 1] = make_float4(Uyf * rf, Uzf * rf, (d2f(Th0) + d2f(Tp)) * rf, d2f(p0 * eos_ratio<true>(Tp * iTh0, a)));
     return;
   }
   const double rho = rho0 + rp;
@@ -242,15 +237,16 @@ __device__ __forceinline__ NodeState<T> gather_node(const VolumeArgs& a, long lo
     z.th = w[3 * Ng + g];
     z.pp = w[4 * Ng + g];
   } else {
-    const float* w = static_cast<const float*>(a.prim);
-    z.Ux = w[g];
-    z.Uy = w[Ng + g];
-    z.Uz = w[2 * Ng + g];
-    z.ux = w[3 * Ng + g];
-    z.uy = w[4 * Ng + g];
-    z.uz = w[5 * Ng + g];
-    z.th = w[6 * Ng + g];
-    z.pp = w[7 * Ng + g];
+    const float4* w = static_cast<const float4*>(a.prim);
+    const float4 p = w[2 * g], r = w[2 * g + 1];
+    z.Ux = p.x;
+    z.Uy = p.y;
+    z.Uz = p.z;
+    z.ux = p.w;
+    z.uy = r.x;
+    z.uz = r.y;
+    z.th = r.z;
+    z.pp = r.w;
   }
   return z;
 }

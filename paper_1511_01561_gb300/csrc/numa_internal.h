@@ -48,7 +48,8 @@ bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const do
 // the stage update (or the primitive pass) for the state the next create_rhs
 // differentiates:
 //   FP64 mode  : double [5][Ng] = u_x, u_y, u_z, theta, p'   (U comes from q)
-//   FP32 mode  : float  [8][Ng] = U_x, U_y, U_z, u_x, u_y, u_z, theta, p'
+//   FP32 mode  : float  [Ng][8] = (U_x, U_y, U_z, u_x), (u_y, u_z, theta, p') per node,
+//                two float4 (one 32-byte sector per node for the gather)
 //   pairs mode : float2 [8][Ng] = the same eight, each as a (hi, lo) pair
 inline int prim_bytes_per_node(int precision) {
   return precision == NUMA_FP32_MIXED ? 32 : precision == NUMA_FP64_PAIRS ? 64 : 40;
