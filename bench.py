@@ -75,12 +75,12 @@ FP64_PEAK_TFLOPS = 1.25
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "fd055b861f803b9f",
-               "volume_fp64_affine": 224.358912e6 + 126.825216e6,
-               "volume_fp64_nodal": 481.542400e6 + 142.580992e6,
-               "volume_fp32_affine": 139.276288e6 + 53.992960e6,
-               "volume_fp32_nodal": 248.955392e6 + 63.062272e6,
-               "volume_pairs_affine": 224.357120e6 + 129.257472e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "0b34af9fc5ddb0c2",
+               "volume_fp64_affine": 224.309504e6 + 125.987072e6,
+               "volume_fp64_nodal": 482.401024e6 + 142.800128e6,
+               "volume_fp32_affine": 139.232768e6 + 49.504512e6,
+               "volume_fp32_nodal": 249.009152e6 + 60.783872e6,
+               "volume_pairs_affine": 224.342272e6 + 129.383168e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
