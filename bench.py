@@ -75,7 +75,7 @@ FP64_PEAK_TFLOPS = 1.25
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "0b34af9fc5ddb0c2",
+NCU_TRAFFIC = {"kernels_sha256_16": "0b34af9fc5ddb0c2", "workload": "bubble_32x32x32_N4",
                "volume_fp64_affine": 224.309504e6 + 125.987072e6,
                "volume_fp64_nodal": 482.401024e6 + 142.800128e6,
                "volume_fp32_affine": 139.232768e6 + 49.504512e6,
@@ -94,8 +94,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(key: str):
-    return NCU_TRAFFIC.get(key) if kernel_source_hash() == NCU_TRAFFIC["kernels_sha256_16"] else None
+def ncu_traffic(key: str, workload: str):
+    """DRAM bytes per launch of a kernel from the committed capture: only for
+    the workload it was captured on, and only while the kernel sources hash
+    to the value they had then."""
+    if workload != NCU_TRAFFIC["workload"] or kernel_source_hash() != NCU_TRAFFIC["kernels_sha256_16"]:
+        return None
+    return NCU_TRAFFIC.get(key)
 
 
 def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
@@ -391,7 +396,7 @@ def run_mine(args):
         "gpu_launches": 2 * nlaunch,
         "roofline": {"kernel": f"volume_kernel<{N},double,{form_name}>", "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": ncu_traffic(f"volume_fp64_{form_name}"),
+                     "traffic": ncu_traffic(f"volume_fp64_{form_name}", args.workload),
                      "algorithmic_flops": flops,
                      "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine),
                      "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
@@ -429,7 +434,7 @@ def run_mine(args):
             "roofline": {"kernel": f"volume_kernel<{N},double,nodal>", "bound": "alu",
                          "achieved": fl_n / voln_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": fl_n / voln_s / 1e12 / FP64_PEAK_TFLOPS,
-                         "traffic": ncu_traffic("volume_fp64_nodal")},
+                         "traffic": ncu_traffic("volume_fp64_nodal", args.workload)},
         }
     if not args.no_fp32:
         ms32, vol32, upd32, _, _, _, fin32, _ = measure("fp32_mixed")
@@ -442,7 +447,7 @@ def run_mine(args):
             "roofline": {"kernel": f"volume_kernel<{N},float,{form_name}>", "bound": "hbm",
                          "achieved": b / vol32_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
                          "frac": b / vol32_s / 1e9 / hbm_gbs,
-                         "traffic": ncu_traffic(f"volume_fp32_{form_name}"), "algorithmic_bytes": b,
+                         "traffic": ncu_traffic(f"volume_fp32_{form_name}", args.workload), "algorithmic_bytes": b,
                          "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
             "update_ms_avg": upd32 / nlaunch,
             "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
@@ -454,7 +459,7 @@ def run_mine(args):
             line["fp32_mixed"]["nodal_form"] = {
                 "value": world * Ng * STAGES * args.steps / (ms32n * 1e-3), "ms_per_step": ms32n / args.steps,
                 "finite": fin32n, "volume_ms_avg": 1e3 * vol32n_s, "volume_hbm_frac": bn / vol32n_s / 1e9 / hbm_gbs,
-                "traffic": ncu_traffic("volume_fp32_nodal")}
+                "traffic": ncu_traffic("volume_fp32_nodal", args.workload)}
     if not args.no_fp32:
         # FP64-accurate element kernel on the FP32 units ((hi, lo) float pairs)
         msp, volp, updp, _, _, _, finp, _ = measure("fp64_pairs")
@@ -465,7 +470,7 @@ def run_mine(args):
             "value": vp, "unit": UNIT, "ms_per_step": msp / args.steps, "speedup_vs_fp64": vp / value,
             "form": form_name, "finite": finp, "volume_ms_avg": 1e3 * volp_s, "update_ms_avg": updp / nlaunch,
             "volume_fp64_equiv_tflops": volume_flops_per_elem_node(N, affine) * Nl / volp_s / 1e12,
-            "volume_traffic": ncu_traffic(f"volume_pairs_{form_name}"),
+            "volume_traffic": ncu_traffic(f"volume_pairs_{form_name}", args.workload),
             "volume_hbm_gbs": bp / volp_s / 1e9, "volume_hbm_frac": bp / volp_s / 1e9 / hbm_gbs,
         }
         if affine:
