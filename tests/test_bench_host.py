@@ -1,0 +1,67 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic byte and flop
+models behind the roofline, the whole-job rate, the command line, and the
+rule that a committed ncu traffic figure is reported only for the workload
+and kernel sources it was captured on."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_flop_models():
+    # per-node form: 39 contractions of N+1 FMAs plus 150 pointwise flops
+    assert bench.volume_flops_per_elem_node(4) == 78 * 5 + 150
+    # affine form: 15 contractions plus 65 pointwise flops
+    assert bench.volume_flops_per_elem_node(4, affine=True) == 30 * 5 + 65
+    assert bench.volume_flops_per_elem_node(1, affine=True) < bench.volume_flops_per_elem_node(1)
+
+
+def test_byte_models():
+    Nl, Ng, N = 4_096_000, 2_146_689, 4
+    # FP64 affine: Jw 8 + l2g 4 + residual 40 per element node, 72 per element, 64 per global node
+    assert bench.volume_bytes(Nl, Ng, 8, N, True) == Nl * 52 + Nl // 125 * 72 + Ng * 64
+    # per-node form reads all ten metric values at every element node
+    assert bench.volume_bytes(Nl, Ng, 8) - bench.volume_bytes(Nl, Ng, 8, N, True) == Nl * 72 - Nl // 125 * 72
+    # the DSS map of CG storage has one entry per element node; DG storage more
+    cg = bench.update_bytes(Nl, Ng, 8, 2 / 3)
+    assert bench.update_bytes(Nl, Ng, 8, 2 / 3, entries=Nl) == cg
+    assert bench.update_bytes(Nl, Nl, 8, 2 / 3, entries=10_941_048) > cg
+
+
+def test_whole_job_rate():
+    # node-updates per RK stage of all replicas: world * Ng * 3 stages * steps / seconds
+    assert bench.whole_job_rate(1, 1000, 10, 1000.0) == pytest.approx(30_000.0)
+    assert bench.whole_job_rate(4, 1000, 10, 1000.0) == pytest.approx(120_000.0)
+
+
+def test_command_line():
+    a = bench.parse_args([])
+    assert (a.gpus, a.impl, a.workload) == (1, "mine", "bubble_32x32x32_N4")
+    assert a.warmup >= 3 and not a.imex_only and not a.no_dg and not a.no_imex
+    b = bench.parse_args(["--imex-only", "--no-dg", "--no-imex", "--steps", "7", "--warmup", "4"])
+    assert b.imex_only and b.no_dg and b.no_imex and (b.steps, b.warmup) == (7, 4)
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--impl", "other"])
+
+
+def test_traffic_only_for_its_workload_and_sources(monkeypatch):
+    wl = bench.NCU_TRAFFIC["workload"]
+    key = "volume_fp64_affine"
+    if bench.kernel_source_hash() == bench.NCU_TRAFFIC["kernels_sha256_16"]:
+        assert bench.ncu_traffic(key, wl) == bench.NCU_TRAFFIC[key]
+    assert bench.ncu_traffic(key, "shell_6x30x30x8_N4") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic(key, wl) is None
+
+
+def test_kernel_source_hash_covers_the_kernel_files():
+    csrc = os.path.join(ROOT, "paper_1511_01561_gb300", "csrc")
+    for name in bench.KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(csrc, name)), name
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
