@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate / saturated request rate")
     p.add_argument("--serve-overload", type=float, default=2.0,
                    help="rate of a second Poisson stream / saturated request rate (0 skips it)")
+    p.add_argument("--peaks", action="store_true",
+                   help="measure the FP64/FP32 FMA and FP64/TF32 mma.sync throughput of the GPU instead")
     return p.parse_args(argv)
 
 
@@ -67,9 +69,12 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# FP64 peak of the GB300 (dense, non-tensor): the nominal 1.25 TFLOP/s of the
-# profiling recipe; a register-only DFMA probe on this pool measured 1.19.
+# FP64 peak of the GB300 (dense, non-tensor): the nominal 1.25 TFLOP/s (152
+# SMs x 2 FP64 FMA per clock x 2070 MHz); `bench.py --peaks` measured 1.258
+# with register-only FMA chains and 1.10 with FP64 mma.sync
+# (profiles/p0_arithmetic_peaks_gb300.md).
 FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_SOURCE = "nominal FP64 FMA rate; measured 1.258 TFLOP/s (profiles/p0_arithmetic_peaks_gb300.md)"
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
@@ -399,7 +404,7 @@ def run_mine(args):
                      "traffic": ncu_traffic(f"volume_fp64_{form_name}", args.workload),
                      "algorithmic_flops": flops,
                      "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine),
-                     "peak_source": "nominal FP64 of the recipe (probe: 1.19)",
+                     "peak_source": FP64_PEAK_SOURCE,
                      "avg_launch_ms": 1e3 * vol_avg_s,
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},
         "kernels": {"volume_ms_avg": 1e3 * vol_avg_s, "update_ms_avg": ms_upd / nlaunch,
@@ -634,10 +639,45 @@ def run_serve(args):
     }))
 
 
+def run_peaks(args):
+    """Throughput of the units an element kernel could run on: FP64 and FP32
+    FMA chains and FP64 / TF32 mma.sync, each a register-only kernel timed
+    with CUDA events (best of three runs of about half a second), with the
+    SM clock sampled by nvidia-smi during the runs."""
+    import torch
+
+    from paper_1511_01561_gb300 import numa
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nbytes = sms * 8 * 256 * 8
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    out = {"metric": "arithmetic throughput per unit", "unit": "TFLOP/s", "sms": sms, "units": {}}
+    for kind in numa.PEAK_KINDS:
+        numa.numa_probe_peak(kind, 16, buf.data_ptr(), nbytes, stream)  # warm-up
+        ms, _ = numa.numa_probe_peak(kind, 1000, buf.data_ptr(), nbytes, stream)
+        iters = max(1000, int(1000 * 500.0 / max(ms, 1e-3)))
+        clocks = ClockSampler(0)
+        runs = [numa.numa_probe_peak(kind, iters, buf.data_ptr(), nbytes, stream) for _ in range(3)]
+        ck = clocks.stop()
+        best = max(r[1] for r in runs)
+        d = {"tflops": best, "runs_tflops": [r[1] for r in runs], "ms": [r[0] for r in runs], "iters": iters,
+             "clocks": ck}
+        if ck and ck.get("sm_mhz"):
+            # flops per SM per clock at the median sampled clock
+            d["flops_per_sm_per_clock"] = best * 1e12 / (sms * ck["sm_mhz"] * 1e6)
+        out["units"][kind] = d
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
     if args.cpu_worker:
         cpu_worker(args)
+    elif args.peaks:
+        run_peaks(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.serve:

@@ -280,6 +280,21 @@ int numa_time_kernels(numa_ctx* ctx, double dt, int nsteps, double* ms_volume, d
  * Waits for the stream. *flag = 0 or 1. */
 int numa_check_finite(numa_ctx* ctx, int* flag);
 
+/* Measurement helper, not part of the method: the arithmetic throughput of
+ * one unit on the current device, from one register-only kernel of `iters`
+ * loop iterations over 8 CTAs of 256 threads per SM, timed with CUDA events
+ * on `stream` (cudaStream_t as void*); waits for it.
+ *   kind 0: FP64 FMA (8 independent chains per thread)
+ *   kind 1: FP32 FMA (8 chains per thread)
+ *   kind 2: FP64 mma.sync m8n8k4 (4 accumulators per warp)
+ *   kind 3: TF32 mma.sync m16n8k8 with FP32 accumulation (4 per warp)
+ * dev_out: device scratch of out_bytes >= SMs * 8 * 256 * (8 bytes for kinds
+ * 0 and 2, 4 for kinds 1 and 3), overwritten (one value per thread).
+ * *ms: kernel time; *tflops: 2 * multiply-adds / time.  NUMA_EINVAL for a bad
+ * kind, iters < 1 or a short buffer. */
+int numa_probe_peak(int kind, int iters, void* dev_out, size_t out_bytes, void* stream, double* ms,
+                    double* tflops);
+
 /* ---- Serving: continuous batching of ensemble members ---------------------
  * Not in the paper: many independent forecasts (members of different mesh
  * sizes, orders, precisions and step counts) share one GPU.  Members advance

@@ -54,48 +54,100 @@ RHS_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
 _lib_handle = None
 
 
+def _load_lib(path: str):
+    """Load an oracle shared library and declare its signatures."""
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.orc_lgl.argtypes = [ctypes.c_int, dp, dp]
+    L.orc_dmatrix.argtypes = [ctypes.c_int, dp, dp]
+    L.orc_build.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)]
+    L.orc_build.restype = ctypes.c_int
+    L.orc_free.argtypes = [ctypes.c_void_p]
+    L.orc_sizes.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_long)] * 3
+    for name in ("orc_get_coords", "orc_get_elem_coords", "orc_get_metrics", "orc_get_jw",
+                 "orc_get_mass", "orc_get_ref"):
+        getattr(L, name).argtypes = [ctypes.c_void_p, dp]
+    L.orc_get_l2g.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_long)]
+    L.orc_get_wall.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte)]
+    L.orc_pprime.argtypes = [ctypes.c_double] * 4
+    L.orc_pprime.restype = ctypes.c_double
+    L.orc_pprime_naive.argtypes = [ctypes.c_double] * 3 + [ctypes.POINTER(_Config)]
+    L.orc_pprime_naive.restype = ctypes.c_double
+    L.orc_init_state.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
+    L.orc_init_state.restype = ctypes.c_int
+    L.orc_rhs_elem.argtypes = [ctypes.c_void_p, dp, dp]
+    L.orc_rhs.argtypes = [ctypes.c_void_p, dp, dp]
+    L.orc_ssprk3_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
+    L.orc_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
+    L.orc_run.restype = ctypes.c_int
+    L.orc_lsrk54_coefficients.argtypes = [dp, dp]
+    L.orc_lsrk54_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
+    L.orc_run_lsrk54.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
+    L.orc_run_lsrk54.restype = ctypes.c_int
+    L.orc_filter_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_filter_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_filter_matrix.restype = ctypes.c_int
+    L.orc_filter.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.orc_filter.restype = ctypes.c_int
+    L.orc_run_filtered.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.orc_run_filtered.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib_handle
     if _lib_handle is None:
         build()
-        L = ctypes.CDLL(_SO)
-        dp = ctypes.POINTER(ctypes.c_double)
-        L.orc_lgl.argtypes = [ctypes.c_int, dp, dp]
-        L.orc_dmatrix.argtypes = [ctypes.c_int, dp, dp]
-        L.orc_build.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)]
-        L.orc_build.restype = ctypes.c_int
-        L.orc_free.argtypes = [ctypes.c_void_p]
-        L.orc_sizes.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_long)] * 3
-        for name in ("orc_get_coords", "orc_get_elem_coords", "orc_get_metrics", "orc_get_jw",
-                     "orc_get_mass", "orc_get_ref"):
-            getattr(L, name).argtypes = [ctypes.c_void_p, dp]
-        L.orc_get_l2g.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_long)]
-        L.orc_get_wall.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte)]
-        L.orc_pprime.argtypes = [ctypes.c_double] * 4
-        L.orc_pprime.restype = ctypes.c_double
-        L.orc_pprime_naive.argtypes = [ctypes.c_double] * 3 + [ctypes.POINTER(_Config)]
-        L.orc_pprime_naive.restype = ctypes.c_double
-        L.orc_init_state.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
-        L.orc_init_state.restype = ctypes.c_int
-        L.orc_rhs_elem.argtypes = [ctypes.c_void_p, dp, dp]
-        L.orc_rhs.argtypes = [ctypes.c_void_p, dp, dp]
-        L.orc_ssprk3_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
-        L.orc_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
-        L.orc_run.restype = ctypes.c_int
-        L.orc_lsrk54_coefficients.argtypes = [dp, dp]
-        L.orc_lsrk54_step.argtypes = [ctypes.c_long, dp, ctypes.c_double, RHS_FN, ctypes.c_void_p, dp]
-        L.orc_run_lsrk54.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int]
-        L.orc_run_lsrk54.restype = ctypes.c_int
-        L.orc_filter_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_filter_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_filter_matrix.restype = ctypes.c_int
-        L.orc_filter.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        L.orc_filter.restype = ctypes.c_int
-        L.orc_run_filtered.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        L.orc_run_filtered.restype = ctypes.c_int
-        _lib_handle = L
+        _lib_handle = _load_lib(_SO)
     return _lib_handle
+
+
+def build_variant(edits, tag: str) -> str:
+    """Compile a copy of the oracle with textual edits [(old, new), ...]
+    applied, each old snippet occurring exactly once.  The tests plant
+    mistakes this way, to show that a pin catches them; the variant goes to
+    a temporary directory, never next to the real oracle."""
+    import tempfile
+
+    with open(_SRC) as f:
+        src = f.read()
+    for old, new in edits:
+        n = src.count(old)
+        if n != 1:
+            raise ValueError(f"edit target occurs {n} times: {old!r}")
+        src = src.replace(old, new)
+    d = tempfile.mkdtemp(prefix=f"orc_{tag}_")
+    c_path = os.path.join(d, "numa_oracle.c")
+    with open(c_path, "w") as f:
+        f.write(src)
+    with open(os.path.join(_HERE, "numa_oracle.h")) as f:
+        hdr = f.read()
+    with open(os.path.join(d, "numa_oracle.h"), "w") as f:
+        f.write(hdr)
+    so = os.path.join(d, "liborc_variant.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-o", so,
+                    c_path, "-lm"], check=True, cwd=d)
+    return so
+
+
+class using_library:
+    """Context manager: every oracle call made inside it (Mesh objects built
+    inside it included) goes to the library at `path`."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib_handle
+        self._saved = lib()
+        _lib_handle = _load_lib(self.path)
+        return _lib_handle
+
+    def __exit__(self, *exc):
+        global _lib_handle
+        _lib_handle = self._saved
+        return False
 
 
 def _dp(a: np.ndarray):
@@ -208,25 +260,26 @@ class Mesh:
     def __init__(self, cfg: dict):
         self.cfg = dict(cfg)
         self._c = make_config(cfg)
+        self._L = lib()  # the library this mesh was built with serves all its calls
         h = ctypes.c_void_p()
-        rc = lib().orc_build(ctypes.byref(self._c), ctypes.byref(h))
+        rc = self._L.orc_build(ctypes.byref(self._c), ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle mesh build failed (rc={rc})")
         self._h = h
         ne, nl, ng = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
-        lib().orc_sizes(h, ctypes.byref(ne), ctypes.byref(nl), ctypes.byref(ng))
+        self._L.orc_sizes(h, ctypes.byref(ne), ctypes.byref(nl), ctypes.byref(ng))
         self.Ne, self.Nl, self.Ng = ne.value, nl.value, ng.value
         self.N = int(cfg["N"])
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_free(h)
+            self._L.orc_free(h)
             self._h = None
 
     def _get(self, name, shape):
         a = np.zeros(shape)
-        getattr(lib(), name)(self._h, _dp(a))
+        getattr(self._L, name)(self._h, _dp(a))
         return a
 
     def coords(self):
@@ -251,19 +304,19 @@ class Mesh:
 
     def l2g(self):
         a = np.zeros(self.Nl, dtype=np.int64)
-        lib().orc_get_l2g(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
+        self._L.orc_get_l2g(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
         return a
 
     def wall(self):
         a = np.zeros(self.Ng, dtype=np.uint8)
-        lib().orc_get_wall(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        self._L.orc_get_wall(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
         return a
 
     def init_state(self, kind: str, params=()) -> np.ndarray:
         q = np.zeros((5, self.Ng))
         p = np.zeros(8)
         p[: len(params)] = params
-        rc = lib().orc_init_state(self._h, IC[kind], _dp(p), _dp(q))
+        rc = self._L.orc_init_state(self._h, IC[kind], _dp(p), _dp(q))
         if rc != 0:
             raise ValueError(f"oracle init_state failed (rc={rc})")
         return q
@@ -271,18 +324,18 @@ class Mesh:
     def rhs_elem(self, q: np.ndarray) -> np.ndarray:
         q = np.ascontiguousarray(q, dtype=np.float64)
         re = np.zeros((5, self.Nl))
-        lib().orc_rhs_elem(self._h, _dp(q), _dp(re))
+        self._L.orc_rhs_elem(self._h, _dp(q), _dp(re))
         return re
 
     def rhs(self, q: np.ndarray) -> np.ndarray:
         q = np.ascontiguousarray(q, dtype=np.float64)
         R = np.zeros((5, self.Ng))
-        lib().orc_rhs(self._h, _dp(q), _dp(R))
+        self._L.orc_rhs(self._h, _dp(q), _dp(R))
         return R
 
     def run(self, q: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
-        rc = lib().orc_run(self._h, _dp(q), dt, nsteps)
+        rc = self._L.orc_run(self._h, _dp(q), dt, nsteps)
         if rc != 0:
             raise MemoryError("oracle run failed")
         return q
@@ -290,20 +343,20 @@ class Mesh:
     def run_lsrk54(self, q: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
         """nsteps steps of the five-stage low-storage RK."""
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
-        if lib().orc_run_lsrk54(self._h, _dp(q), dt, nsteps) != 0:
+        if self._L.orc_run_lsrk54(self._h, _dp(q), dt, nsteps) != 0:
             raise MemoryError("oracle run failed")
         return q
 
     def filter(self, q: np.ndarray, s: int, p: float, mu: float = 1.0) -> np.ndarray:
         """One application of the Boyd-Vandeven filter with DSS (Sec. 6 loop)."""
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
-        if lib().orc_filter(self._h, _dp(q), s, p, mu) != 0:
+        if self._L.orc_filter(self._h, _dp(q), s, p, mu) != 0:
             raise ValueError("oracle filter failed")
         return q
 
     def run_filtered(self, q: np.ndarray, dt: float, nsteps: int, every: int, s: int, p: float,
                      mu: float = 1.0) -> np.ndarray:
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
-        if lib().orc_run_filtered(self._h, _dp(q), dt, nsteps, every, s, p, mu) != 0:
+        if self._L.orc_run_filtered(self._h, _dp(q), dt, nsteps, every, s, p, mu) != 0:
             raise ValueError("oracle filtered run failed")
         return q

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libnuma_gb300.so")
 # the element kernels of each precision are separate units so that they
 # compile in parallel
 SOURCES = ["mesh.cpp", "imex_setup.cpp", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu", "filter.cu", "imex.cu",
-           "numa_api.cu", "noalloc.cu", "serve.cu"]
+           "numa_api.cu", "noalloc.cu", "serve.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code (the mesh and geometry setup) is compiled without floating-point
 # contraction so that node coordinates come out bitwise the same on x86-64

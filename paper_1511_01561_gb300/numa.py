@@ -84,6 +84,7 @@ def _load():
         "numa_sched_result": [vp, ctypes.c_longlong, dp, ctypes.c_longlong],
         "numa_sched_cancel": [vp, ctypes.c_longlong],
         "numa_sched_destroy": [vp],
+        "numa_probe_peak": [i, i, vp, ctypes.c_size_t, vp, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -213,6 +214,17 @@ def numa_check_finite(ctx) -> int:
     f = ctypes.c_int()
     _check(ctx, lib.numa_check_finite(ctx, ctypes.byref(f)))
     return f.value
+
+
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma_m8n8k4": 2, "tf32_mma_m16n8k8": 3}
+
+
+def numa_probe_peak(kind: str, iters: int, out_ptr: int, out_bytes: int, stream_ptr: int):
+    """(ms, TFLOP/s) of one register-only throughput kernel of the given unit."""
+    ms, tf = ctypes.c_double(), ctypes.c_double()
+    _check(None, lib.numa_probe_peak(PEAK_KINDS[kind], int(iters), ctypes.c_void_p(out_ptr), int(out_bytes),
+                                     ctypes.c_void_p(stream_ptr), ctypes.byref(ms), ctypes.byref(tf)))
+    return ms.value, tf.value
 
 
 def numa_get_coords(ctx) -> np.ndarray:

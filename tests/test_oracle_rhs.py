@@ -278,3 +278,158 @@ def test_isothermal_rest_about_isentropic_reference_converges(orc):
         inner = m.wall() == 0
         errs.append(np.abs(R[3][inner]).max() / (g * np.abs(q[0]).max()))
     assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10, errs
+
+
+# ------------------------------------------ deep-atmosphere shell terms ----
+# The source of Eq. 1 on the rotating sphere (Sec. 1: deep-atmosphere
+# equations, no shallow-atmosphere approximation): Coriolis -2 Omega z x U and
+# buoyancy along the radial gravity g(r) = g0 (a/r)^2, and the hydrostatic
+# reference state in that gravity.  Each pin below also runs on copies of the
+# oracle with a plausible mistake planted in its C source, and must fail
+# there.
+
+CORIOLIS = ("S[1] = -rp * gr * x / r + 2.0 * c->Omega * q[2 * Ng + g];\n"
+            "            S[2] = -rp * gr * y / r - 2.0 * c->Omega * q[1 * Ng + g];")
+GRAVITY = "double gr = c->g * (c->r_inner / r) * (c->r_inner / r);"
+GEOPOTENTIAL = "return c->g * c->r_inner * h / (c->r_inner + h);"
+
+PLANTED = {
+    # +2 Omega z x U (both signs flipped)
+    "coriolis_sign": [(CORIOLIS, "S[1] = -rp * gr * x / r - 2.0 * c->Omega * q[2 * Ng + g];\n"
+                                 "            S[2] = -rp * gr * y / r + 2.0 * c->Omega * q[1 * Ng + g];")],
+    # -Omega z x U (factor 2 dropped)
+    "coriolis_factor": [(CORIOLIS, "S[1] = -rp * gr * x / r + c->Omega * q[2 * Ng + g];\n"
+                                   "            S[2] = -rp * gr * y / r - c->Omega * q[1 * Ng + g];")],
+    # each component taken from the wrong momentum component
+    "coriolis_transposed": [(CORIOLIS, "S[1] = -rp * gr * x / r + 2.0 * c->Omega * q[1 * Ng + g];\n"
+                                       "            S[2] = -rp * gr * y / r - 2.0 * c->Omega * q[2 * Ng + g];")],
+    # shallow (constant) gravity in the buoyancy
+    "gravity_constant": [(GRAVITY, "double gr = c->g;")],
+    # g0 a / r instead of g0 (a/r)^2
+    "gravity_power": [(GRAVITY, "double gr = c->g * (c->r_inner / r);")],
+    # geopotential of constant gravity in the reference state
+    "geopotential_flat": [(GEOPOTENTIAL, "return c->g * h;")],
+}
+
+
+@pytest.fixture(scope="module")
+def planted(orc):
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            cache[name] = orc.build_variant(PLANTED[name], name)
+        return cache[name]
+
+    return get
+
+
+def _rhat(m):
+    xyz = m.coords()
+    return xyz / np.linalg.norm(xyz, axis=0)
+
+
+def _coriolis_error(orc):
+    """max |R_U(Omega) - R_U(0) - P (2 Omega (U_y, -U_x, 0))| relative to
+    max |2 Omega U| for rho' = Theta' = 0 and a smooth U; P removes the radial
+    component at the bottom and lid nodes (the wall condition)."""
+    cfg = I.shell(2, 2, 4)
+    Om = cfg["Omega"]
+    m1, m0 = orc.Mesh(cfg), orc.Mesh(dict(cfg, Omega=0.0))
+    xyz = m1.coords()
+    rho0 = m1.ref()[0]
+    q = np.zeros((5, m1.Ng))
+    q[1:4] = I.smooth_perturbation(xyz, seed=41, length=3.0e6, U=1.0)[1:4] * 10.0 * rho0
+    d = m1.rhs(q)[1:4] - m0.rhs(q)[1:4]
+    exact = 2.0 * Om * np.array([q[2], -q[1], np.zeros(m1.Ng)])
+    walls = (m1.wall() & 8) != 0
+    rh = _rhat(m1)
+    exact[:, walls] -= (exact[:, walls] * rh[:, walls]).sum(0) * rh[:, walls]
+    assert np.abs(exact).max() > 1e-4  # a Coriolis tendency of size
+    return np.abs(d - exact).max() / np.abs(exact).max()
+
+
+def test_coriolis_closed_form(orc):
+    """The rotation enters R only through -2 Omega z x U: the difference of
+    the tendencies with and without rotation is that term, at every node."""
+    assert _coriolis_error(orc) < 1e-12
+
+
+def _gravity_error(orc):
+    """rho' != 0, U = 0, Theta' = 0: every flux vanishes exactly, so
+    R_rho = R_Theta = 0 and R_U = -rho' g0 (a/r)^2 r_hat (Eq. 4: the DSS of a
+    nodal source is the source), with the radial part removed at the bottom
+    and lid.  Returns the largest relative deviation."""
+    cfg = I.shell(2, 2, 4)
+    m = orc.Mesh(cfg)
+    rho0 = m.ref()[0]
+    q = np.zeros((5, m.Ng))
+    q[0] = 0.01 * rho0 * I.smooth_perturbation(m.coords(), seed=42, length=3.0e6, rho=1.0)[0]
+    R = m.rhs(q)
+    assert np.all(R[0] == 0.0) and np.all(R[4] == 0.0)
+    r = np.linalg.norm(m.coords(), axis=0)
+    g = cfg["g"] * (cfg["r_inner"] / r) ** 2
+    exact = -q[0] * g * _rhat(m)
+    walls = (m.wall() & 8) != 0
+    scale = np.abs(exact).max()
+    err_in = np.abs(R[1:4][:, ~walls] - exact[:, ~walls]).max() / scale
+    err_wall = np.abs(R[1:4][:, walls]).max() / scale  # a purely radial tendency is removed
+    return max(err_in, err_wall)
+
+
+def test_deep_gravity_buoyancy_closed_form(orc):
+    assert _gravity_error(orc) < 1e-13
+
+
+def _column_balance_error(orc, cfg):
+    """Along one radial column of the shell, the reference state satisfies
+    dp0/dr = -rho0 g0 (a/r)^2 (hydrostatic balance in the deep-atmosphere
+    gravity).  dp0/dr is taken from a Chebyshev fit of the oracle's p0 at the
+    column's nodes; returns the largest relative deviation."""
+    m = orc.Mesh(cfg)
+    xyz = m.coords()
+    r = np.linalg.norm(xyz, axis=0)
+    rh = xyz / r
+    k = int(np.argmax(rh[2]))  # the column through the node nearest the pole
+    col = np.where(np.abs(rh - rh[:, [k]]).max(axis=0) < 1e-12)[0]
+    assert len(col) == cfg["nlayer"] * cfg["N"] + 1
+    o = col[np.argsort(r[col])]
+    rho0, _, p0 = m.ref()
+    h = r[o] - cfg["r_inner"]
+    fit = np.polynomial.Chebyshev.fit(h, p0[o], 24)
+    dpdr = fit.deriv()(h)
+    exact = -rho0[o] * cfg["g"] * (cfg["r_inner"] / r[o]) ** 2
+    return np.abs(dpdr - exact).max() / np.abs(exact).max()
+
+
+SHELL_REFS = [
+    I.shell(1, 12, 6),  # isothermal 250 K to 30 km (the shell workloads' reference)
+    I.shell(1, 12, 6, ref="isentropic", theta0=300.0, r_outer=I.EARTH_RADIUS + 10.0e3),
+]
+
+
+@pytest.mark.parametrize("cfg", SHELL_REFS, ids=["isothermal", "isentropic"])
+def test_shell_reference_is_hydrostatic(orc, cfg):
+    assert _column_balance_error(orc, cfg) < 1e-9
+    m = orc.Mesh(cfg)
+    _, th0, p0 = m.ref()
+    peos = cfg["P00"] * (cfg["Rd"] * th0 / cfg["P00"]) ** _gamma(cfg)
+    np.testing.assert_allclose(peos, p0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("mistake", ["coriolis_sign", "coriolis_factor", "coriolis_transposed"])
+def test_coriolis_pin_catches_planted_mistakes(orc, planted, mistake):
+    with orc.using_library(planted(mistake)):
+        assert _coriolis_error(orc) > 1e-3
+
+
+@pytest.mark.parametrize("mistake", ["gravity_constant", "gravity_power"])
+def test_gravity_pin_catches_planted_mistakes(orc, planted, mistake):
+    with orc.using_library(planted(mistake)):
+        assert _gravity_error(orc) > 1e-4
+
+
+def test_reference_pin_catches_flat_geopotential(orc, planted):
+    with orc.using_library(planted("geopotential_flat")):
+        assert _column_balance_error(orc, SHELL_REFS[0]) > 1e-4
+        assert _column_balance_error(orc, SHELL_REFS[1]) > 1e-4
