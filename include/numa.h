@@ -2,7 +2,7 @@
  * numa.h -- C ABI of the GB300-native CG spectral-element RHS / Runge-Kutta
  * hot path of the NUMA dynamical core (Mueller et al., "Strong scaling for
  * numerical weather prediction at petascale with the atmospheric model
- * NUMA", Sec. 2 and the main loop of code example 1 in Sec. 6).
+ * NUMA", Sec. 2 and the main loop of code example 1 in Sec. 7).
  *
  * Ownership model
  *   - The library allocates no device memory.  The caller provides one device
@@ -88,7 +88,7 @@ enum numa_ic_kind { NUMA_IC_REST = 0, NUMA_IC_BUBBLE = 1, NUMA_IC_UNIFORM = 2, N
  *   applied after the derivative). */
 typedef enum { NUMA_METRIC_AUTO = 0, NUMA_METRIC_NODAL = 1 } numa_metric_form;
 
-/* Storage of the node data (Sec. 5's comparison of CG and DG storage).
+/* Storage of the node data (Sec. 6's comparison of CG and DG storage).
  * CG: one value per global node; element nodes that coincide share it and
  *   the element kernel gathers through the element-to-global map.
  * DG: one value per element node (Ng = Nl in numa_mesh_info): every element
@@ -171,18 +171,24 @@ int numa_rhs(numa_ctx* ctx, const double* q_dev, double* r_dev);
 /* Size of the library-owned scratch used by numa_rhs_static_scratch. */
 #define NUMA_STATIC_SCRATCH_BYTES (16u << 20)
 
-/* The paper has no counterpart to this call; it exists for callers that
- * cannot allocate device memory (code running during CUDA graph capture,
- * allocation-free real-time loops, plug-ins handed only input and output
- * buffers).  Same result as numa_rhs, but its scratch -- the primitive fields
- * (40 bytes per global node) and the element residuals (40 bytes per element
- * node in FP64, 20 in FP32-mixed) -- lives in a fixed 16 MiB device array
- * inside the library (NUMA_STATIC_SCRATCH_BYTES; about 2,200 elements at N=4)
- * instead of the bound workspace, and nothing is allocated.  Larger meshes
- * return NUMA_EINVAL.  The first call on a device looks up the array's device
- * address; make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the
- * GPU race.  q_dev, r_dev: device double[5][Ng], enqueued on the bound stream. */
+/* The paper has no counterpart to this call.  It is for callers that cannot
+ * allocate device memory: real-time loops that forbid allocation once they
+ * run, and plug-ins whose host application owns all device memory and hands
+ * them only input and output buffers.  Same result as numa_rhs, bit for bit,
+ * but its scratch -- the primitive fields and the element residuals -- lives
+ * in a fixed 16 MiB device array inside the library
+ * (NUMA_STATIC_SCRATCH_BYTES) instead of the bound workspace, and nothing is
+ * allocated: no cudaMalloc, no cudaFree, no allocating library call.
+ * Scratch per global node: 40 bytes (FP64), 32 (FP32-mixed), 64 (pairs); per
+ * element node: 40 (FP64, pairs) or 20 (FP32-mixed).  At N=4 the largest
+ * cubic boxes that fit are 12^3 elements (FP64, pairs) and 15^3 (FP32-mixed);
+ * larger meshes return NUMA_EINVAL with the bytes needed in
+ * numa_last_error.  The first call in each CUDA context (normally one per
+ * device) looks up the array's device address and caches it; make that first
+ * call before any stream capture.  Every call shares the one array and leaves
+ * its contents behind: calls whose work overlaps on the GPU (other streams,
+ * other contexts) race on it.  q_dev, r_dev: device double[5][Ng] (may not
+ * alias), enqueued on the bound stream. */
 int numa_rhs_static_scratch(numa_ctx* ctx, const double* q_dev, double* r_dev);
 
 /* Advance the context's state by one step of size dt of the selected
@@ -242,7 +248,7 @@ int numa_set_time_scheme(numa_ctx* ctx, int scheme);
  * (default 0.05; 0 turns it off).  NUMA_EINVAL outside that range. */
 int numa_set_robert_asselin(numa_ctx* ctx, double nu);
 
-/* Boyd-Vandeven filter (Sec. 2.3), applied as in the time loop of Sec. 6:
+/* Boyd-Vandeven filter (Sec. 2.3), applied as in the time loop of Sec. 7:
  * after every `every`-th step of numa_run / numa_rk_step (the count restarts
  * at numa_set_filter, numa_set_state and numa_init_state), the state becomes
  *   q <- M^-1 DSS(Jw (F x F x F) q_e),
@@ -288,8 +294,11 @@ int numa_check_finite(numa_ctx* ctx, int* flag);
  *   kind 1: FP32 FMA (8 chains per thread)
  *   kind 2: FP64 mma.sync m8n8k4 (4 accumulators per warp)
  *   kind 3: TF32 mma.sync m16n8k8 with FP32 accumulation (4 per warp)
+ *   kind 4: half the warps as kind 0, half as kind 2, sized to take equal
+ *           time alone: a total near the sum of the two rates means the two
+ *           FP64 paths run side by side
  * dev_out: device scratch of out_bytes >= SMs * 8 * 256 * (8 bytes for kinds
- * 0 and 2, 4 for kinds 1 and 3), overwritten (one value per thread).
+ * 0, 2 and 4; 4 for kinds 1 and 3), overwritten (one value per thread).
  * *ms: kernel time; *tflops: 2 * multiply-adds / time.  NUMA_EINVAL for a bad
  * kind, iters < 1 or a short buffer. */
 int numa_probe_peak(int kind, int iters, void* dev_out, size_t out_bytes, void* stream, double* ms,

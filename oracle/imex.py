@@ -1,5 +1,5 @@
 """1D-IMEX oracle: leapfrog steps with implicit corrections along vertical
-columns (Sec. 2.2, the time loop of Sec. 6), in plain numpy, FP64.
+columns (Sec. 2.2, the time loop of Sec. 7), in plain numpy, FP64.
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
 CPU-baseline leg of the benchmark may import this module.  It shares no code
@@ -207,7 +207,7 @@ def run_imex(mesh: O.Mesh, q0: np.ndarray, dt: float, nsteps: int, nu: float, co
 def run_imex_filtered(mesh: O.Mesh, q0: np.ndarray, dt: float, nsteps: int, nu: float, every: int, s: int,
                       p: float, mu: float, cols: VerticalColumns = None):
     """The 1D-IMEX leapfrog with the Boyd-Vandeven filter after every
-    `every`-th step, as the time loop of Sec. 6 orders them: the IMEX
+    `every`-th step, as the time loop of Sec. 7 orders them: the IMEX
     correction (and the Robert-Asselin average, which takes the unfiltered
     q^{n+1}), then the filter of q^{n+1} with DSS and M^-1.  Returns
     (q^nsteps, filtered q^{nsteps-1})."""

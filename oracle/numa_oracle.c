@@ -2,7 +2,7 @@
  * numa_oracle.c -- plain FP64 CPU oracle of the NUMA CG spectral-element
  * right-hand side, direct stiffness summation, inverse mass matrix and
  * SSP-RK3 stage (Mueller et al., Sec. 2 "Numerical Methods", Eqs. 1-5, and
- * the main loop of code example 1 in Sec. 6).
+ * the main loop of code example 1 in Sec. 7).
  *
  * TEST INFRASTRUCTURE ONLY: the reference the CUDA path is checked against.
  * It shares no code with the GPU library and is never called by it.
@@ -770,7 +770,7 @@ int orc_run(const orc_mesh* m, double* q, double dt, int nsteps) {
 }
 
 /* ---------------------------------------------------------------------- */
-/* Filter (Sec. 2.3 and the time loop of Sec. 6)                            */
+/* Filter (Sec. 2.3 and the time loop of Sec. 7)                            */
 /* ---------------------------------------------------------------------- */
 
 /* Boyd-Vandeven filter weights of the Legendre modes k = 0..N: Vandeven's
@@ -873,7 +873,7 @@ int orc_filter_matrix(int N, int s, double p, double mu, double* F) {
 }
 
 /* One application of the filter to the global state q (in place), as the
- * time loop of Sec. 6 states it: per element, the tensor product F x F x F
+ * time loop of Sec. 7 states it: per element, the tensor product F x F x F
  * on the element-node values of each variable; then DSS of the Jw-weighted
  * element values in ascending element-node order and division by M.  At wall
  * nodes the wall-normal momentum component keeps its value from before the

@@ -348,7 +348,7 @@ class Mesh:
         return q
 
     def filter(self, q: np.ndarray, s: int, p: float, mu: float = 1.0) -> np.ndarray:
-        """One application of the Boyd-Vandeven filter with DSS (Sec. 6 loop)."""
+        """One application of the Boyd-Vandeven filter with DSS (Sec. 7 loop)."""
         q = np.ascontiguousarray(q, dtype=np.float64).copy()
         if self._L.orc_filter(self._h, _dp(q), s, p, mu) != 0:
             raise ValueError("oracle filter failed")

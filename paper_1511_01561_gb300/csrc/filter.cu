@@ -1,5 +1,5 @@
 // Element part of the Boyd-Vandeven filter (Sec. 2.3), applied after a time
-// step as in the time loop of Sec. 6: per element the tensor product
+// step as in the time loop of Sec. 7: per element the tensor product
 // F x F x F of the 1D modal filter on the five state variables.  The kernel
 // writes the Jw-weighted correction Jw ((F x F x F) q - q) into the residual
 // buffer; mode 3 of the update kernel then forms q + M^-1 DSS(correction),

@@ -1,6 +1,6 @@
 // Column part of the 1D-IMEX leapfrog step (Sec. 2.2: an explicit leapfrog
 // step, then implicit corrections along each vertical column of grid points;
-// the IMEX line of the time loop in Sec. 6), for the z-columns of a box and
+// the IMEX line of the time loop in Sec. 7), for the z-columns of a box and
 // the radial columns of the cubed-sphere shell.
 //
 // With the explicit tendency R = R(q^n) already in memory, per column:

@@ -441,7 +441,7 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
   return true;
 }
 
-// DG storage (the paper's Sec. 5 comparison of CG, DG and CG/DG storage):
+// DG storage (the paper's Sec. 6 comparison of CG, DG and CG/DG storage):
 // every element node keeps its own copy of the node data.  The expanded mesh
 // has Nl storage nodes, l2g the identity, and per-node arrays (coordinates,
 // reference state, M^-1, wall flags, shell vectors) copied from each element

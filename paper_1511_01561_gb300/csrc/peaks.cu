@@ -86,17 +86,52 @@ __global__ void __launch_bounds__(kThreads) tf32_chains(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Half of the warps run FP64 FMA chains, the other half FP64 mma.sync: shows
+// whether the two FP64 paths share one pipe (the total stays near either
+// rate alone) or run side by side (it approaches their sum).
+__global__ void __launch_bounds__(kThreads) fp64_fma_and_mma(double* out, int iters_fma, int iters_mma) {
+  double s = 0.0;
+  if ((threadIdx.x >> 5) & 1) {
+    double acc[kAcc][2];
+#pragma unroll
+    for (int c = 0; c < kAcc; ++c) acc[c][0] = acc[c][1] = 0.0;
+    const double a = 1e-3 * (1 + (threadIdx.x & 3)), b = 1e-3;
+    for (int i = 0; i < iters_mma; ++i) {
+#pragma unroll
+      for (int c = 0; c < kAcc; ++c) dmma_884(acc[c][0], acc[c][1], a, b);
+    }
+#pragma unroll
+    for (int c = 0; c < kAcc; ++c) s += acc[c][0] + acc[c][1];
+  } else {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = double(threadIdx.x + c) * 1e-3;
+    for (int i = 0; i < iters_fma; ++i) {
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], 0.999999, 1e-6);
+    }
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" int numa_probe_peak(int kind, int iters, void* dev_out, size_t out_bytes, void* stream, double* ms,
                                double* tflops) {
-  if (!ms || !tflops || !dev_out || iters < 1 || kind < 0 || kind > 3) return NUMA_EINVAL;
+  if (!ms || !tflops || !dev_out || iters < 1 || kind < 0 || kind > 4) return NUMA_EINVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NUMA_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NUMA_ECUDA;
   const unsigned blocks = (unsigned)(sms * kBlocksPerSM);
   const size_t threads = (size_t)blocks * kThreads;
-  const size_t elem = (kind == 0 || kind == 2) ? 8 : 4;
+  const size_t elem = (kind == 1 || kind == 3) ? 4 : 8;
+  // kind 4: an FMA thread does 16 flops per iteration, an mma thread 64; with
+  // the rates of each path alone (1.26 and 1.10 TFLOP/s) both halves take the
+  // same time when the mma warps run 16/64 * 1.10/1.26 of the iterations
+  const int iters_fma = iters;
+  const int iters_mma = (int)(iters * 0.2186) > 1 ? (int)(iters * 0.2186) : 1;
   if (out_bytes < threads * elem) return NUMA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -108,7 +143,8 @@ extern "C" int numa_probe_peak(int kind, int iters, void* dev_out, size_t out_by
       case 0: fma_chains<double><<<blocks, kThreads, 0, s>>>((double*)dev_out, iters, 0.999999, 1e-6); break;
       case 1: fma_chains<float><<<blocks, kThreads, 0, s>>>((float*)dev_out, iters, 0.9999f, 1e-4f); break;
       case 2: dmma_chains<<<blocks, kThreads, 0, s>>>((double*)dev_out, iters); break;
-      default: tf32_chains<<<blocks, kThreads, 0, s>>>((float*)dev_out, iters); break;
+      case 3: tf32_chains<<<blocks, kThreads, 0, s>>>((float*)dev_out, iters); break;
+      default: fp64_fma_and_mma<<<blocks, kThreads, 0, s>>>((double*)dev_out, iters_fma, iters_mma); break;
     }
     e = cudaGetLastError();
   }
@@ -126,7 +162,10 @@ extern "C" int numa_probe_peak(int kind, int iters, void* dev_out, size_t out_by
     case 0:
     case 1: per_thread_iter = 2.0 * kChains; break;
     case 2: per_thread_iter = 2.0 * 8 * 8 * 4 * kAcc / 32.0; break;
-    default: per_thread_iter = 2.0 * 16 * 8 * 8 * kAcc / 32.0; break;
+    case 3: per_thread_iter = 2.0 * 16 * 8 * 8 * kAcc / 32.0; break;
+    default:  // half the threads each way, flops of both halves over the one kernel time
+      per_thread_iter = 0.5 * (2.0 * kChains + 2.0 * 8 * 8 * 4 * kAcc / 32.0 * iters_mma / (double)iters_fma);
+      break;
   }
   *ms = t;
   *tflops = per_thread_iter * (double)iters * (double)threads / (t * 1e-3) / 1e12;

@@ -216,7 +216,8 @@ def numa_check_finite(ctx) -> int:
     return f.value
 
 
-PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma_m8n8k4": 2, "tf32_mma_m16n8k8": 3}
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma_m8n8k4": 2, "tf32_mma_m16n8k8": 3,
+              "fp64_fma_with_mma": 4}
 
 
 def numa_probe_peak(kind: str, iters: int, out_ptr: int, out_bytes: int, stream_ptr: int):

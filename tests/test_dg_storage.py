@@ -1,4 +1,4 @@
-"""DG storage of the node data (Sec. 5 compares CG, DG and CG/DG storage).
+"""DG storage of the node data (Sec. 6 compares CG, DG and CG/DG storage).
 
 CPU part: the expanded mesh that numa_create builds for DG storage, checked
 against the CG mesh through the host coordinates: one storage node per

@@ -1,5 +1,5 @@
 """GPU parity of the Boyd-Vandeven filter (Sec. 2.3, applied with DSS and the
-inverse mass matrix as in the time loop of Sec. 6) against the oracle,
+inverse mass matrix as in the time loop of Sec. 7) against the oracle,
 through the C ABI: one application on walled, periodic, warped and shell
 meshes in every precision, and a filtered SSP-RK3 run."""
 import numpy as np

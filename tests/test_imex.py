@@ -192,7 +192,7 @@ def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp64_pairs"])
 def test_imex_with_the_filter(numa, orc, precision):
     """The Boyd-Vandeven filter after every second step, after the IMEX
-    correction as in the time loop of Sec. 6."""
+    correction as in the time loop of Sec. 7."""
     from oracle import imex
 
     cfg, ic, dt = THIN, ("bubble", THIN_BUBBLE), 0.4

@@ -1,5 +1,5 @@
 """Pins of the oracle's Boyd-Vandeven filter (Sec. 2.3, applied with DSS and
-the inverse mass matrix after each time step as in the time loop of Sec. 6).
+the inverse mass matrix after each time step as in the time loop of Sec. 7).
 
 The weights are checked against closed-form values, the symmetry of the
 erfc-log form and Vandeven's original filter (a regularized incomplete beta
