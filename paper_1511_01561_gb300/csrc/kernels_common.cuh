@@ -299,85 +299,6 @@ __device__ __forceinline__ void stage_fluxes_affine(const VolumeArgs& a, long lo
   }
 }
 
-// create_rhs of element e of one mesh, by the whole CTA (one thread per
-// element node); smem_raw holds kNF*(N+1)^3 + (N+1)^2 values of T.  Shared by
-// the single-mesh kernel and the ragged multi-member kernel, so that a member
-// computes bit for bit the same alone and in a mix.
-template <int N, typename T>
-__device__ __forceinline__ void volume_element(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
-  constexpr int P = N + 1, NP = P * P * P;
-  T* F = reinterpret_cast<T*>(smem_raw);  // [kNF][NP]
-  T* Ds = F + kNF * NP;                     // [P][P]
-  const T* Dg;
-  const T* met;
-  if constexpr (sizeof(T) == 8) {
-    Dg = reinterpret_cast<const T*>(a.D64);
-    met = reinterpret_cast<const T*>(a.met64);
-  } else {
-    Dg = reinterpret_cast<const T*>(a.D32);
-    met = reinterpret_cast<const T*>(a.met32);
-  }
-  const int l = threadIdx.x;
-  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
-  const long long n = (long long)e * NP + l;
-  const long long Nl = a.Nl;
-  if (l < NP) stage_fluxes<N, T>(a, n, l, F);
-  __syncthreads();
-  if (l >= NP) return;
-  const int i = l % P, j = (l / P) % P, k = l / (P * P);
-  T dx[P], dy[P], dz[P];
-#pragma unroll
-  for (int m = 0; m < P; ++m) {
-    dx[m] = Ds[i * P + m];
-    dy[m] = Ds[j * P + m];
-    dz[m] = Ds[k * P + m];
-  }
-  // metric terms B[3d+c] = d xi_d / d x_c and Jw (Eq. 5)
-  T B[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + n];
-  const T jw = met[9 * Nl + n];
-  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
-  // reference-space derivatives of field f along xi, eta, zeta (Eq. 5)
-  auto dref = [&](int f, T& s0, T& s1, T& s2) {
-    const T* Ff = F + f * NP;
-    s0 = s1 = s2 = T(0);
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      s0 = fma(dx[m], Ff[bx + m], s0);
-      s1 = fma(dy[m], Ff[by + P * m], s1);
-      s2 = fma(dz[m], Ff[bz + P * P * m], s2);
-    }
-  };
-  // physical derivative along x_c by the chain rule
-  auto phys = [&](int c, T s0, T s1, T s2) { return fma(s0, B[c], fma(s1, B[3 + c], s2 * B[6 + c])); };
-  T s0, s1, s2;
-  T div_r, div_x, div_y, div_z, div_t;
-  dref(kUx, s0, s1, s2); div_r = phys(0, s0, s1, s2);
-  dref(kUy, s0, s1, s2); div_r += phys(1, s0, s1, s2);
-  dref(kUz, s0, s1, s2); div_r += phys(2, s0, s1, s2);
-  dref(kTxx, s0, s1, s2); div_x = phys(0, s0, s1, s2);
-  dref(kTxy, s0, s1, s2); div_x += phys(1, s0, s1, s2); div_y = phys(0, s0, s1, s2);
-  dref(kTxz, s0, s1, s2); div_x += phys(2, s0, s1, s2); div_z = phys(0, s0, s1, s2);
-  dref(kTyy, s0, s1, s2); div_y += phys(1, s0, s1, s2);
-  dref(kTyz, s0, s1, s2); div_y += phys(2, s0, s1, s2); div_z += phys(1, s0, s1, s2);
-  dref(kTzz, s0, s1, s2); div_z += phys(2, s0, s1, s2);
-  dref(kPp, s0, s1, s2);
-  div_x += phys(0, s0, s1, s2);
-  div_y += phys(1, s0, s1, s2);
-  div_z += phys(2, s0, s1, s2);
-  dref(kHx, s0, s1, s2); div_t = phys(0, s0, s1, s2);
-  dref(kHy, s0, s1, s2); div_t += phys(1, s0, s1, s2);
-  dref(kHz, s0, s1, s2); div_t += phys(2, s0, s1, s2);
-  // element residual -Jw div F (Eq. 4); the sources are added per global node
-  T* re = static_cast<T*>(a.re);
-  re[n] = -(jw * div_r);
-  re[Nl + n] = -(jw * div_x);
-  re[2 * Nl + n] = -(jw * div_y);
-  re[3 * Nl + n] = -(jw * div_z);
-  re[4 * Nl + n] = -(jw * div_t);
-}
-
 // create_rhs of an affine element (see stage_fluxes_affine), one thread per
 // element node: each equation's divergence is three contractions with D of
 // the staged contravariant fluxes, 15 per node instead of 39.  The element's
@@ -446,6 +367,173 @@ template <int N>
 __host__ __device__ constexpr int line_group() {
   constexpr int P2 = (N + 1) * (N + 1), NT = ((N + 1) * P2 + 31) / 32 * 32, W32 = (P2 + 31) / 32 * 32;
   return 3 * W32 <= NT ? W32 : P2;
+}
+
+// ---- FP64 element kernels with fewer FP64 instructions ---------------------
+// GB300 issues 2 FP64 FMAs per SM per clock, so the FP64 element kernels are
+// bound by their FP64 instruction count.  Exact rearrangements cut it:
+//
+// (1) Per-node form (any element): the pressure is added into the diagonal
+//     momentum fluxes before they are differentiated (12 fields instead of
+//     13) and the metric terms are stored pre-multiplied by -Jw, so the chain
+//     rule is three FMAs per use of a field and no final weighting remains.
+// (2) Rectilinear affine elements (every element of an unwarped box): the
+//     metric terms dxi_d/dx_c vanish for c != d and, with J constant over the
+//     element, -Jw dxi_d/dx_d at node (i,j,k) is K_d w_j w_k for d = 0 (and
+//     likewise for d = 1, 2) with K_d = -J dxi_d/dx_d per element.  Folding
+//     w_i into D (Dw_im = w_i D_im) and the rest into the staged fluxes gives
+//     the weighted residual -Jw div F of Eq. 4 directly from 15 contractions,
+//     with no metric or Jw load per node.
+
+// Flux fields of the FP64 per-node kernel: F_U = U (x) u + p' I with the
+// pressure in the diagonal components (the symmetric part stored once).
+enum : int { lUx = 0, lUy, lUz, lTxx, lTyy, lTzz, lTxy, lTxz, lTyz, lHx, lHy, lHz, kLF };
+
+// create_rhs of element e in FP64, per-node form of Eq. 5 (any element,
+// curved included), one thread per element node.  The metric terms arrive
+// pre-multiplied by -Jw (rows 0..8 of met64 hold -Jw dxi_d/dx_c for this
+// form), and the pressure sits in the diagonal momentum fluxes, so each of
+// the 12 staged flux fields (kLF) is differentiated along xi, eta and zeta
+// (15 FMAs) and folded into the divergence of every equation that uses it
+// with three FMAs: 9 + 180 + 45 FP64 operations per node at N = 4.  The
+// result is the weighted residual -Jw div F of Eq. 4.  smem_raw holds
+// 12 (N+1)^3 + (N+1)^2 doubles.
+template <int N>
+__device__ __forceinline__ void volume_element_nodal64(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  double* F = reinterpret_cast<double*>(smem_raw);  // [kLF][NP]
+  double* Ds = F + kLF * NP;                         // [P][P]
+  const double* met = a.met64;
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = a.D64[t];
+  const long long Nl = a.Nl, n = (long long)e * NP + l;
+  double B[9];  // -Jw dxi_d/dx_c at this node, [3d + c]
+  if (l < NP) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + n];
+    const NodeState<double> z = gather_node<double>(a, n);
+    F[lUx * NP + l] = z.Ux;
+    F[lUy * NP + l] = z.Uy;
+    F[lUz * NP + l] = z.Uz;
+    F[lTxx * NP + l] = fma(z.Ux, z.ux, z.pp);
+    F[lTyy * NP + l] = fma(z.Uy, z.uy, z.pp);
+    F[lTzz * NP + l] = fma(z.Uz, z.uz, z.pp);
+    F[lTxy * NP + l] = z.Ux * z.uy;
+    F[lTxz * NP + l] = z.Ux * z.uz;
+    F[lTyz * NP + l] = z.Uy * z.uz;
+    F[lHx * NP + l] = z.th * z.Ux;
+    F[lHy * NP + l] = z.th * z.Uy;
+    F[lHz * NP + l] = z.th * z.Uz;
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  double dx[P], dy[P], dz[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    dx[m] = Ds[i * P + m];
+    dy[m] = Ds[j * P + m];
+    dz[m] = Ds[k * P + m];
+  }
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  // reference-space derivatives of field f along xi, eta, zeta (Eq. 5)
+  auto dref = [&](int f, double& s0, double& s1, double& s2) {
+    const double* Ff = F + f * NP;
+    s0 = dx[0] * Ff[bx];
+    s1 = dy[0] * Ff[by];
+    s2 = dz[0] * Ff[bz];
+#pragma unroll
+    for (int m = 1; m < P; ++m) {
+      s0 = fma(dx[m], Ff[bx + m], s0);
+      s1 = fma(dy[m], Ff[by + P * m], s1);
+      s2 = fma(dz[m], Ff[bz + P * P * m], s2);
+    }
+  };
+  // chain rule into the weighted divergence: acc += -Jw d/dx_c of the field
+  auto first = [&](int c, double s0, double s1, double s2) { return fma(s2, B[6 + c], fma(s1, B[3 + c], s0 * B[c])); };
+  auto add = [&](double& acc, int c, double s0, double s1, double s2) {
+    acc = fma(s2, B[6 + c], fma(s1, B[3 + c], fma(s0, B[c], acc)));
+  };
+  double s0, s1, s2, dr, dxm, dym, dzm, dt;
+  dref(lUx, s0, s1, s2); dr = first(0, s0, s1, s2);
+  dref(lUy, s0, s1, s2); add(dr, 1, s0, s1, s2);
+  dref(lUz, s0, s1, s2); add(dr, 2, s0, s1, s2);
+  dref(lTxx, s0, s1, s2); dxm = first(0, s0, s1, s2);
+  dref(lTyy, s0, s1, s2); dym = first(1, s0, s1, s2);
+  dref(lTzz, s0, s1, s2); dzm = first(2, s0, s1, s2);
+  dref(lTxy, s0, s1, s2); add(dxm, 1, s0, s1, s2); add(dym, 0, s0, s1, s2);
+  dref(lTxz, s0, s1, s2); add(dxm, 2, s0, s1, s2); add(dzm, 0, s0, s1, s2);
+  dref(lTyz, s0, s1, s2); add(dym, 2, s0, s1, s2); add(dzm, 1, s0, s1, s2);
+  dref(lHx, s0, s1, s2); dt = first(0, s0, s1, s2);
+  dref(lHy, s0, s1, s2); add(dt, 1, s0, s1, s2);
+  dref(lHz, s0, s1, s2); add(dt, 2, s0, s1, s2);
+  double* re = static_cast<double*>(a.re);
+  re[n] = dr;
+  re[Nl + n] = dxm;
+  re[2 * Nl + n] = dym;
+  re[3 * Nl + n] = dzm;
+  re[4 * Nl + n] = dt;
+}
+
+// create_rhs of a rectilinear affine element in FP64 (see (2) above), one
+// thread per element node.  Node (i,j,k) stages, for each direction d, the
+// fluxes of the five equations along x_d scaled by beta_d = K_d w w (the two
+// Lobatto weights of the other directions):
+//   mass  beta_d U_d,  momentum beta_d U_c u_d (+ beta_d p' for c = d),
+//   Theta theta beta_d U_d,
+// and the weighted residual of equation v at (i,j,k) is then
+//   sum_m Dw_im G_v0(m,j,k) + sum_m Dw_jm G_v1(i,m,k) + sum_m Dw_km G_v2(i,j,m).
+// a.affk holds K_d per element [3][Ne], a.Dw64 Dw [P][P], a.ww64 w_i w_j
+// [P][P].  Shared memory: 15 (N+1)^3 + (N+1)^2 doubles.
+template <int N>
+__device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  double* G = reinterpret_cast<double*>(smem_raw);  // [15][NP]
+  double* Ds = G + 15 * NP;                         // [P][P]
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = a.Dw64[t];
+  const long long Nl = a.Nl, e0 = (long long)e * NP, n = e0 + l;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  if (l < NP) {
+    const double K0 = a.affk[e], K1 = a.affk[a.Ne + e], K2 = a.affk[2 * (long long)a.Ne + e];
+    const NodeState<double> z = gather_node<double>(a, n);
+    const double bt[3] = {K0 * a.ww64[j * P + k], K1 * a.ww64[i * P + k], K2 * a.ww64[i * P + j]};
+    const double U[3] = {z.Ux, z.Uy, z.Uz}, u[3] = {z.ux, z.uy, z.uz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double Gr = bt[d] * U[d], ud = bt[d] * u[d], pd = bt[d] * z.pp;
+      G[d * NP + l] = Gr;
+      G[(3 + d) * NP + l] = d == 0 ? fma(z.Ux, ud, pd) : z.Ux * ud;
+      G[(6 + d) * NP + l] = d == 1 ? fma(z.Uy, ud, pd) : z.Uy * ud;
+      G[(9 + d) * NP + l] = d == 2 ? fma(z.Uz, ud, pd) : z.Uz * ud;
+      G[(12 + d) * NP + l] = z.th * Gr;
+    }
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  double dx[P], dy[P], dz[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    dx[m] = Ds[i * P + m];
+    dy[m] = Ds[j * P + m];
+    dz[m] = Ds[k * P + m];
+  }
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  double* re = static_cast<double*>(a.re);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double* g0 = G + (3 * v) * NP;
+    const double* g1 = g0 + NP;
+    const double* g2 = g1 + NP;
+    double t = dx[0] * g0[bx];
+#pragma unroll
+    for (int m = 1; m < P; ++m) t = fma(dx[m], g0[bx + m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dy[m], g1[by + P * m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dz[m], g2[bz + P * P * m], t);
+    re[v * Nl + n] = t;
+  }
 }
 
 // create_rhs of element e in the FP32 form, organised by 1D lines of nodes
@@ -814,6 +902,7 @@ constexpr size_t element_smem_bytes() {
   constexpr int P = N + 1, NP = P * P * P;
   if constexpr (std::is_same<T, float>::value) return sizeof(float) * (kNF > 15 ? kNF : 15) * NP;
   if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (15 * NP + P * P);
+  if constexpr (std::is_same<T, double>::value) return sizeof(T) * (kLF * NP + P * P);
   if constexpr (AFF) return sizeof(T) * (15 * NP + P * P + 15);
   return sizeof(T) * (kNF * NP + P * P + kNF);
 }
@@ -824,9 +913,15 @@ __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, un
   if constexpr (std::is_same<T, Pairs>::value) {
     if constexpr (AFF) volume_element_pairs_affine<N>(a, e, smem_raw);
     else volume_element_pairs<N>(a, e, smem_raw);
-  } else if constexpr (std::is_same<T, float>::value) volume_element_lines<N, AFF>(a, e, smem_raw);
-  else if constexpr (AFF) volume_element_affine<N, T>(a, e, smem_raw);
-  else volume_element<N, T>(a, e, smem_raw);
+  } else if constexpr (std::is_same<T, float>::value) {
+    volume_element_lines<N, AFF>(a, e, smem_raw);
+  } else if constexpr (AFF) {
+    // uniform over the CTA: rectilinear elements take the folded form
+    if (a.affine == 2) volume_element_rect<N>(a, e, smem_raw);
+    else volume_element_affine<N, T>(a, e, smem_raw);
+  } else {
+    volume_element_nodal64<N>(a, e, smem_raw);
+  }
 }
 
 template <int N, typename T, bool AFF>

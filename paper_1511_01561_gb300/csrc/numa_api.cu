@@ -1,6 +1,6 @@
 // C-ABI of the GB300 NUMA hot path (declared in include/numa.h): context
 // life cycle, workspace binding, state I/O and the stage loop of code
-// example 1 in Sec. 6 (create_rhs, DSS with the inverse mass matrix, update
+// example 1 in Sec. 7 (create_rhs, DSS with the inverse mass matrix, update
 // q), with one CUDA graph per RK step for numa_run.
 #include <cmath>
 #include <cstring>
@@ -64,10 +64,13 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.met2 = c->L.met2;
   a.D2 = c->L.D2;
   a.re = re;
+  a.affk = c->L.affk;
+  a.Dw64 = c->L.Dw64;
+  a.ww64 = c->L.ww64;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
-  a.affine = affine_elements(c->cfg) ? 1 : 0;
+  a.affine = affine_elements(c->cfg) ? (c->rect ? 2 : 1) : 0;
   return a;
 }
 
@@ -307,6 +310,29 @@ cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s, cudaEvent_t*
   return cudaSuccess;
 }
 
+// The per-node FP64 form reads -Jw dxi_d/dx_c: rows 0..8 of the uploaded
+// metric array times -Jw (row 9), in place.
+__global__ void __launch_bounds__(256) weight_metric_kernel(double* met, long long Nl) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= Nl) return;
+  const double mjw = -met[9 * Nl + n];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) met[t * Nl + n] *= mjw;
+}
+
+// Whether every element has diagonal metric terms (off-diagonal entries
+// exactly zero at its first node): the elements of an affine mesh are then
+// rectilinear.
+bool rectilinear_elements(const HostMesh& m) {
+  const long long Nl = m.Nl, Np = m.Np;
+  for (long long e = 0; e < m.Ne; ++e) {
+    const long long n = e * Np;
+    for (int t : {1, 2, 3, 5, 6, 7})
+      if (m.met[t * Nl + n] != 0.0) return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 namespace numa {
@@ -344,6 +370,11 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
     d.nrm = (double*)take(3 * Ng * 8);
   }
   d.D64 = (double*)take(PP * 8);
+  if (c.precision == NUMA_FP64 && affine_elements(c)) {
+    d.affk = (double*)take(3 * (size_t)m.Ne * 8);
+    d.Dw64 = (double*)take(PP * 8);
+    d.ww64 = (double*)take(PP * 8);
+  }
   d.D32 = (float*)take(PP * 4);
   d.D2 = (float2*)take(PP * 8);
   d.F64 = (double*)take(PP * 8);
@@ -477,6 +508,37 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.D32, D32.data(), D32.size() * 4);
   up(L.D2, D2.data(), D2.size() * 4);
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
+  // FP64: the weighted metric of the per-node form, or the per-element
+  // constants of rectilinear elements
+  std::vector<double> affk, Dw, ww;
+  bool rect = false;
+  if (c->cfg.precision == NUMA_FP64) {
+    if (!affine_elements(c->cfg)) {
+      if (e == cudaSuccess && Nl)
+        weight_metric_kernel<<<(unsigned)((Nl + 255) / 256), 256, 0, s>>>(L.met64, (long long)Nl);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    } else {
+      const int P = m.P;
+      rect = rectilinear_elements(m);
+      affk.assign(3 * (size_t)m.Ne, 0.0);
+      const double w0 = m.w[0];
+      for (long long el = 0; el < m.Ne; ++el) {
+        const long long n = el * m.Np;
+        const double J = m.met[9 * Nl + n] / (w0 * w0 * w0);
+        for (int d = 0; d < 3; ++d) affk[d * (size_t)m.Ne + el] = -J * m.met[(4 * d) * Nl + n];
+      }
+      Dw.resize((size_t)P * P);
+      ww.resize((size_t)P * P);
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+          Dw[i * P + j] = m.w[i] * m.D[i * P + j];
+          ww[i * P + j] = m.w[i] * m.w[j];
+        }
+      up(L.affk, affk.data(), affk.size() * 8);
+      up(L.Dw64, Dw.data(), Dw.size() * 8);
+      up(L.ww64, ww.data(), ww.size() * 8);
+    }
+  }
   up(L.l2g, m.l2g.data(), Nl * 4);
   up(L.csr_off, m.csr_off.data(), (Ng + 1) * 4);
   up(L.csr_idx, m.csr_idx.data(), m.csr_idx.size() * 4);
@@ -492,6 +554,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind upload");
   c->L = L;
+  c->rect = rect;
   // kernel attributes are set outside any stream capture
   VolumeArgs probe = volume_args(c, L.q, L.prim, L.re);
   probe.Ne = 0;

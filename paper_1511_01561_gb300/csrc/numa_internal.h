@@ -61,7 +61,8 @@ struct DevLayout {
   double* qs = nullptr;      // stage state [5][Ng]
   void* prim = nullptr;      // primitive fields (scratch) [kPrimBytesPerNode * Ng]
   void* re = nullptr;        // element residuals -Jw div F (scratch): double or float [5][Nl]
-  double* met64 = nullptr;   // [10][Nl] FP64 metric terms and Jw
+  double* met64 = nullptr;   // [10][Nl] FP64 metric terms and Jw; for the per-node form rows 0..8
+                             // hold -Jw dxi_d/dx_c (the weighted metric of volume_element_nodal64)
   float* met32 = nullptr;    // [10][Nl] FP32 copy (mixed-precision form)
   float2* met2 = nullptr;    // [10][Nl] (hi, lo) pairs (pairs mode)
   float2* D2 = nullptr;      // [P*P] (hi, lo) pairs (pairs mode)
@@ -75,6 +76,9 @@ struct DevLayout {
   double* gvec = nullptr;    // [3][Ng] (shell)
   double* nrm = nullptr;     // [3][Ng] (shell)
   double* D64 = nullptr;     // [P*P]
+  double* affk = nullptr;    // FP64 affine elements: [3][Ne] K_d = -J dxi_d/dx_d per element
+  double* Dw64 = nullptr;    // FP64 affine elements: [P*P] w_i D_ij
+  double* ww64 = nullptr;    // FP64 affine elements: [P*P] w_i w_j
   float* D32 = nullptr;      // [P*P]
   double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
@@ -117,9 +121,14 @@ struct VolumeArgs {
   const float2* met2;  // pairs mode
   const float2* D2;    // pairs mode
   void* re;            // [5][Nl] output
+  const double* affk;  // FP64 rectilinear form: [3][Ne] -J dxi_d/dx_d
+  const double* Dw64;  // FP64 rectilinear form: w_i D_ij
+  const double* ww64;  // FP64 rectilinear form: w_i w_j
   long long Ng, Nl;
   int Ne;
-  int affine;          // 1: every element is affine, the kernel takes the contravariant-flux form
+  int affine;          // 0: per-node form; 1: every element is affine, the kernel takes the
+                       // contravariant-flux form; 2: every element is also rectilinear (diagonal
+                       // metric terms), FP64 takes the folded form (volume_element_rect)
 };
 
 struct UpdateArgs {
@@ -267,6 +276,7 @@ struct numa_ctx {
   numa::DevLayout L;
   bool bound = false;
   bool prim_valid = false;  // L.prim holds the primitive fields of L.q
+  bool rect = false;        // FP64, affine and every element rectilinear: the folded element kernel
   cudaStream_t stream = nullptr;
   std::string err;
   double gamma = 1.4;

@@ -1,5 +1,5 @@
-// Element kernels (Eq. 4 / Eq. 5) in FP64: per-node and affine-element forms,
-// single-mesh and ragged multi-member launches.
+// Element kernels (Eq. 4 / Eq. 5) in FP64: the per-node, affine-element and
+// rectilinear forms, single-mesh and ragged multi-member launches.
 #include "kernels_common.cuh"
 
 namespace numa {
