@@ -54,6 +54,10 @@ def parse_args(argv=None):
     p.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate / saturated request rate")
     p.add_argument("--serve-overload", type=float, default=2.0,
                    help="rate of a second Poisson stream / saturated request rate (0 skips it)")
+    p.add_argument("--no-shell", action="store_true", help="skip the cubed-sphere shell block")
+    p.add_argument("--no-serve-block", action="store_true", help="skip the reduced serving block")
+    p.add_argument("--serve-block-requests", type=int, default=16)
+    p.add_argument("--serve-block-steps-scale", type=float, default=0.1)
     p.add_argument("--peaks", action="store_true",
                    help="measure the FP64/FP32 FMA and FP64/TF32 mma.sync throughput of the GPU instead")
     return p.parse_args(argv)
@@ -110,12 +114,17 @@ def ncu_traffic(key: str, workload: str):
 
 def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
     """Algorithmic flops per element node of create_rhs (an FMA counts 2).
-    Per-node form of Eq. 5: 39 contractions of length N+1 plus about 150
-    pointwise flops.  Affine-element form: 15 contractions of length N+1 plus
-    65 pointwise flops (per direction: B_d.u and B_d.U, 5 each; three momentum
-    fluxes U_x (B_d.u) + B_dx p', 3 each; theta (B_d.U), 1; then 5 products
-    with -Jw)."""
-    return 30.0 * (N + 1) + 65.0 if affine else 78.0 * (N + 1) + 150.0
+    Per-node form of Eq. 5: the flux tensor has 12 distinct components (U,
+    the symmetric U (x) u + p' I, theta U), each differentiated along the
+    three reference directions (36 contractions of length N+1, 72 (N+1)
+    flops); the chain rule folds each of the 15 uses of a derivative triple
+    into its equation (15 x 3 multiply-adds, 90 flops); building the fluxes
+    takes 12 flops and the -Jw weights 5: 72 (N+1) + 107.  Affine-element
+    form: 15 contractions of length N+1 plus 65 pointwise flops (per
+    direction: B_d.u and B_d.U, 5 each; three momentum fluxes
+    U_x (B_d.u) + B_dx p', 3 each; theta (B_d.U), 1; then 5 products with
+    -Jw)."""
+    return 30.0 * (N + 1) + 65.0 if affine else 72.0 * (N + 1) + 107.0
 
 
 def filter_flops_per_elem_node(N: int) -> float:
@@ -327,28 +336,30 @@ def run_mine(args):
             dist.destroy_process_group()
         return
 
-    def measure(precision, form="auto", scheme="ssp3", storage="cg"):
-        s = numa.Solver(dict(cfg, metric_form=form, storage=storage), precision, device=str(dev))
+    def measure(precision, form="auto", scheme="ssp3", storage="cg", wl=None):
+        wl = w if wl is None else wl
+        s = numa.Solver(dict(wl["cfg"], metric_form=form, storage=storage), precision, device=str(dev))
         s.set_time_scheme(scheme)
-        s.init_state(*w["ic"])
-        s.run(dt, args.warmup)
+        s.init_state(*wl["ic"])
+        s.run(wl["dt"], args.warmup)
         stream = s.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(local) if (precision, form, scheme) == ("fp64", "auto", "ssp3") else None
+        headline = (precision, form, scheme) == ("fp64", "auto", "ssp3") and wl is w
+        clocks = ClockSampler(local) if headline else None
         e0.record(stream)
-        s.run(dt, args.steps)
+        s.run(wl["dt"], args.steps)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
         ms = max_ranks(e0.elapsed_time(e1))
         ck = clocks.stop() if clocks else None
         # per-kernel device times over the same number of steps (event-bracketed launches)
-        ms_vol, ms_upd = s.time_kernels(dt, args.steps)
+        ms_vol, ms_upd = s.time_kernels(wl["dt"], args.steps)
         info = s.info
         e2e = None
-        if not args.no_e2e and (precision, form, scheme) == ("fp64", "auto", "ssp3"):
+        if not args.no_e2e and headline:
             q_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             out_host = torch.empty((5, s.Ng), dtype=torch.float64, pin_memory=True)
             s.get_state(q_host)
@@ -365,7 +376,7 @@ def run_mine(args):
             e2e = {"value": world * s.Ng * STAGES * args.steps / te, "unit": UNIT,
                    "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
         filt = None
-        if (precision, form, scheme) == ("fp64", "auto", "ssp3") and args.filter_reps > 0:
+        if headline and args.filter_reps > 0:
             # Boyd-Vandeven filter (element kernel + DSS update), applied on its own
             s.set_filter(0, max(0, w["cfg"]["N"] - 1), 12.0, 1.0)
             s.filter()
@@ -502,6 +513,31 @@ def run_mine(args):
                 / upd_s / 1e9 / hbm_gbs}
     if not args.no_imex:
         line["imex"] = imex_block(args, numa, torch, dev, barrier, max_ranks)
+    if not args.no_shell and args.workload != "shell_6x30x30x8_N4":
+        # the deep-atmosphere shell (curved elements, per-node form of Eq. 5)
+        ws = I.WORKLOADS["shell_6x30x30x8_N4"]
+        sh = {"workload": "shell_6x30x30x8_N4", "unit": UNIT, "steps": args.steps, "dt": ws["dt"],
+              "form": "per-node (curved elements)"}
+        for prec in ("fp64", "fp32_mixed", "fp64_pairs"):
+            if prec != "fp64" and args.no_fp32:
+                continue
+            mss, vols, upds, infos, _, _, fins, _ = measure(prec, wl=ws)
+            nl = STAGES * args.steps
+            sh[prec] = {"value": whole_job_rate(world, infos["Ng"], args.steps, mss), "ms_per_step": mss / args.steps,
+                        "volume_ms_avg": vols / nl, "update_ms_avg": upds / nl, "finite": fins}
+            if prec == "fp64":
+                fl_s = volume_flops_per_elem_node(infos["N"], False) * infos["Nl"]
+                sh[prec]["roofline"] = {"kernel": f"volume_kernel<{infos['N']},double,nodal>", "bound": "alu",
+                                        "achieved": fl_s / (vols * 1e-3 / nl) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                        "unit": "TFLOP/s",
+                                        "frac": fl_s / (vols * 1e-3 / nl) / 1e12 / FP64_PEAK_TFLOPS}
+            if prec == "fp32_mixed":
+                b32 = volume_bytes(infos["Nl"], infos["Ng"], 4)
+                sh[prec]["speedup_vs_fp64"] = sh[prec]["value"] / sh["fp64"]["value"]
+                sh[prec]["volume_hbm_frac"] = b32 / (vols * 1e-3 / nl) / 1e9 / hbm_gbs
+        line["shell"] = sh
+    if not args.no_serve_block and world == 1:
+        line["serving"] = serving_block(args, numa, torch)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -562,24 +598,13 @@ def imex_block(args, numa, torch, dev, barrier, max_ranks):
     return out
 
 
-def run_serve(args):
-    """Ensemble serving: a seeded stream of rising-bubble forecast requests
-    (edge 8..48 elements, N in {3, 4, 6}, 100..1000 steps, FP64 or FP32-mixed)
-    served with continuous batching.  First all requests at once (saturated
-    request rate), then a Poisson stream at serve_load times that rate, then
-    one at serve_overload times it (the same arrival gaps, rescaled);
-    reports p50/p99 time-to-forecast and aggregate node-updates/s."""
-    import torch
-
-    from paper_1511_01561_gb300 import inputs as I
-    from paper_1511_01561_gb300 import numa
-
-    torch.cuda.set_device(0)
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(args.serve_budget_frac * free) // 256 * 256
-    reqs = I.serving_stream(n=args.serve_requests)
-    for r in reqs:
-        r["nsteps"] = max(1, int(round(r["nsteps"] * args.serve_steps_scale)))
+def serve_streams(numa, reqs, budget, load, overload=0.0, build_threads=8):
+    """Serve `reqs` (inputs.serving_stream) with continuous batching: first
+    all at once (the saturated request rate), then a Poisson stream at `load`
+    times that rate, then (overload > 0) the same arrival gaps at `overload`
+    times it.  Per stream: makespan, p50/p99 time-to-forecast (arrival to
+    result on the host), aggregate node-updates/s, most members at once."""
+    import numpy as np
 
     def node_count(cfg):
         return (cfg["ne"][0] * cfg["N"] + 1) * (cfg["ne"][1] * cfg["N"] + 1) * (cfg["ne"][2] * cfg["N"] + 1)
@@ -587,7 +612,7 @@ def run_serve(args):
     work = sum(node_count(r["cfg"]) * STAGES * r["nsteps"] for r in reqs)
 
     def serve(arrivals):
-        sched = numa.Scheduler(budget, build_threads=min(8, os.cpu_count() or 1))
+        sched = numa.Scheduler(budget, build_threads=build_threads)
         t0 = time.perf_counter()
         pending = sorted(range(len(reqs)), key=lambda i: arrivals[i])
         ids, done_at, max_active = {}, {}, 0
@@ -613,18 +638,66 @@ def run_serve(args):
                     node_updates_per_s=work / makespan, max_active=max_active,
                     failed=sum(st == "failed" for st in statuses))
 
-    import numpy as np
-
     sat = serve([0.0] * len(reqs))
-    rate = args.serve_load * len(reqs) / sat["makespan_s"]
+    rate = load * len(reqs) / sat["makespan_s"]
     gaps = np.array([r["gap"] for r in reqs]) / rate
     arr = list(np.cumsum(gaps) - gaps[0])
     poi = serve(arr)
     over = None
-    if args.serve_overload > 0:
-        scale = args.serve_load / args.serve_overload
-        over = serve([t * scale for t in arr])
-        over["load"] = args.serve_overload
+    if overload > 0:
+        over = serve([t * load / overload for t in arr])
+        over["load"] = overload
+    return dict(saturated=sat, poisson=poi, overload=over, rate=rate, work=work)
+
+
+def serving_budget(torch, frac: float) -> int:
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    return int(frac * free) // 256 * 256
+
+
+def serving_block(args, numa, torch):
+    """A reduced copy of the serving workload inside the default line: the
+    first serve_block_requests requests of the seeded stream, step counts
+    scaled by serve_block_steps_scale, saturated then Poisson at serve_load
+    times the saturated request rate."""
+    from paper_1511_01561_gb300 import inputs as I
+
+    reqs = I.serving_stream(n=args.serve_block_requests)
+    for r in reqs:
+        r["nsteps"] = max(1, int(round(r["nsteps"] * args.serve_block_steps_scale)))
+    budget = serving_budget(torch, args.serve_budget_frac)
+    out = serve_streams(numa, reqs, budget, args.serve_load, 0.0, min(8, os.cpu_count() or 1))
+    poi = out["poisson"]
+    return {"metric": "time-to-forecast p50/p99 (s) and aggregate node-updates/s", "p50_s": poi["p50_s"],
+            "p99_s": poi["p99_s"], "node_updates_per_s": poi["node_updates_per_s"], "unit": UNIT,
+            "config": {"workload": "bubble ensemble stream", "requests": len(reqs), "seed": 1511,
+                       "steps_scale": args.serve_block_steps_scale, "arena_bytes": budget,
+                       "poisson_rate_per_s": out["rate"], "load": args.serve_load,
+                       "fp32_mixed_requests": sum(r["precision"] == "fp32_mixed" for r in reqs),
+                       "total_node_updates": out["work"]},
+            "saturated": out["saturated"], "poisson": poi}
+
+
+def run_serve(args):
+    """Ensemble serving: a seeded stream of rising-bubble forecast requests
+    (edge 8..48 elements, N in {3, 4, 6}, 100..1000 steps, FP64 or FP32-mixed)
+    served with continuous batching.  First all requests at once (saturated
+    request rate), then a Poisson stream at serve_load times that rate, then
+    one at serve_overload times it (the same arrival gaps, rescaled);
+    reports p50/p99 time-to-forecast and aggregate node-updates/s."""
+    import torch
+
+    from paper_1511_01561_gb300 import inputs as I
+    from paper_1511_01561_gb300 import numa
+
+    torch.cuda.set_device(0)
+    budget = serving_budget(torch, args.serve_budget_frac)
+    reqs = I.serving_stream(n=args.serve_requests)
+    for r in reqs:
+        r["nsteps"] = max(1, int(round(r["nsteps"] * args.serve_steps_scale)))
+    out = serve_streams(numa, reqs, budget, args.serve_load, args.serve_overload, min(8, os.cpu_count() or 1))
+    poi = out["poisson"]
     print(json.dumps({
         "metric": "ensemble time-to-forecast p50/p99 and aggregate node-updates/s", "unit": "s",
         "p50": poi["p50_s"], "p99": poi["p99_s"], "value": poi["node_updates_per_s"],
@@ -632,10 +705,10 @@ def run_serve(args):
         "config": {"workload": "bubble ensemble stream", "requests": len(reqs), "seed": 1511,
                    "edge": [8, 48], "N": [3, 4, 6], "steps_scale": args.serve_steps_scale,
                    "arena_bytes": budget, "arena_frac_of_free": args.serve_budget_frac,
-                   "poisson_rate_per_s": rate, "load": args.serve_load,
+                   "poisson_rate_per_s": out["rate"], "load": args.serve_load,
                    "fp32_mixed_requests": sum(r["precision"] == "fp32_mixed" for r in reqs),
-                   "total_node_updates": work},
-        "saturated": sat, "poisson": poi, "overload": over,
+                   "total_node_updates": out["work"]},
+        "saturated": out["saturated"], "poisson": poi, "overload": out["overload"],
     }))
 
 

@@ -959,6 +959,90 @@ __device__ __forceinline__ void dss_node(const UpdateArgs& a, long long I, doubl
   }
 }
 
+// Element nodes at lattice index x along one axis of a CG box with ne
+// elements of order N along it: one (element, local index) pair inside an
+// element, two on a face between elements (and at a periodic seam), sorted by
+// element, then local index; returned as their parts se*e + sl*i of the
+// element-node index.
+__device__ __forceinline__ int axis_nodes(unsigned x, unsigned N, unsigned ne, int per, unsigned se, unsigned sl,
+                                          unsigned (&o)[2]) {
+  const unsigned q = x / N, r = x - q * N;
+  if (r != 0) {
+    o[0] = q * se + r * sl;
+    return 1;
+  }
+  if (!per) {
+    if (q == 0) {
+      o[0] = 0;
+      return 1;
+    }
+    if (q == ne) {  // the far wall
+      o[0] = (ne - 1) * se + N * sl;
+      return 1;
+    }
+    o[0] = (q - 1) * se + N * sl;
+    o[1] = q * se;
+    return 2;
+  }
+  const unsigned qm = q == 0 ? ne - 1 : q - 1;  // periodic: x < ne N, the seam wraps
+  if (qm < q) {
+    o[0] = qm * se + N * sl;
+    o[1] = q * se;
+  } else {  // qm > q, or qm == q (one element along the axis): (q, 0) first
+    o[0] = q * se;
+    o[1] = qm * se + N * sl;
+  }
+  return 2;
+}
+
+// Direct stiffness summation at global node I of a CG box, with the element
+// nodes found from the structured numbering (g = ix + nx (iy + ny iz), element
+// e = ex + nex (ey + ney ez), local l = i + P (j + P k), element node
+// n = e (N+1)^3 + l) instead of the inverse map: the same terms summed in the
+// same ascending element-node order as dss_node, so the sums are identical.
+// Where the axis-by-axis order is not ascending overall (possible only with
+// single-element periodic axes) the node falls back to the inverse map.  The
+// host enables this only for meshes with fewer than 2^31 element nodes.
+template <typename RT>
+__device__ __forceinline__ void dss_box(const UpdateArgs& a, long long I, double (&s)[5]) {
+  const unsigned N = (unsigned)a.box_N, P = N + 1, NP = P * P * P;
+  const unsigned nex = (unsigned)a.box_ne[0], ney = (unsigned)a.box_ne[1];
+  const unsigned nx = (unsigned)a.box_n[0], ny = (unsigned)a.box_n[1];
+  const unsigned u = (unsigned)I, t = u / nx, ix = u - t * nx, iz = t / ny, iy = t - iz * ny;
+  unsigned xo[2], yo[2], zo[2];
+  const int cx = axis_nodes(ix, N, nex, a.box_per[0], NP, 1, xo);
+  const int cy = axis_nodes(iy, N, ney, a.box_per[1], nex * NP, P, yo);
+  const int cz = axis_nodes(iz, N, (unsigned)a.box_ne[2], a.box_per[2], nex * ney * NP, P * P, zo);
+  bool ascending = true;
+  unsigned prev = 0;
+  bool any = false;
+  for (int zc = 0; zc < cz; ++zc)
+    for (int yc = 0; yc < cy; ++yc)
+      for (int xc = 0; xc < cx; ++xc) {
+        const unsigned n = zo[zc] + yo[yc] + xo[xc];
+        ascending &= !any || n > prev;
+        prev = n;
+        any = true;
+      }
+  if (!ascending) {
+    dss_node<RT>(a, I, s);
+    return;
+  }
+  const long long Nl = a.Nl;
+  bool first = true;
+  for (int zc = 0; zc < cz; ++zc)
+    for (int yc = 0; yc < cy; ++yc)
+      for (int xc = 0; xc < cx; ++xc) {
+        const long long n = zo[zc] + yo[yc] + xo[xc];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double r = re_load<RT>(a.re, v * Nl + n);
+          s[v] = first ? r : s[v] + r;
+        }
+        first = false;
+      }
+}
+
 // Everything after the DSS at global node I, given its sums s0..s4.
 template <int MODE, bool SHELL>
 __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long I, double s0, double s1, double s2,
@@ -1088,8 +1172,9 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
 // block's precomputed order (nodes sorted by their number of element nodes,
 // so that the lanes of a warp loop equally often) and leaves the sums in
 // shared memory; the rest runs in natural order (coalesced).  Each node's
-// sum is the same as update_node's, bit for bit.
-template <int MODE, bool SHELL, typename RT>
+// sum is the same as update_node's, bit for bit.  BOX: a CG box, whose DSS
+// finds the element nodes from the structured numbering (dss_box).
+template <int MODE, bool SHELL, typename RT, bool BOX = false>
 __global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
   __shared__ double sums[5][kDssBlock];
   const long long base = (long long)blockIdx.x * kDssBlock;
@@ -1098,7 +1183,8 @@ __global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
     const long long IA = base + lt;
     if (IA < a.Ng) {
       double s[5];
-      dss_node<RT>(a, IA, s);
+      if constexpr (BOX) dss_box<RT>(a, IA, s);
+      else dss_node<RT>(a, IA, s);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sums[v][lt] = s[v];
     }

@@ -102,6 +102,16 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   a.mode = mode;
   a.flag = c->L.flags;
   a.pa = prim_args(c, nullptr, c->L.prim);
+  a.box_N = 0;
+  if (c->cfg.mesh_kind == NUMA_MESH_BOX && c->cfg.storage == NUMA_STORAGE_CG && c->mesh.Nl < (1LL << 31)) {
+    const int ne[3] = {c->cfg.nex, c->cfg.ney, c->cfg.nez};
+    a.box_N = c->mesh.N;
+    for (int d = 0; d < 3; ++d) {
+      a.box_ne[d] = ne[d];
+      a.box_per[d] = c->cfg.periodic[d] ? 1 : 0;
+      a.box_n[d] = (long long)ne[d] * c->mesh.N + (c->cfg.periodic[d] ? 0 : 1);
+    }
+  }
   return a;
 }
 

@@ -154,6 +154,11 @@ struct UpdateArgs {
                        // write the primitives of out)
   int* flag;           // non-finite flag
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
+  // CG box meshes: the lattice of the structured global numbering (g = ix +
+  // nx (iy + ny iz)), from which the DSS finds the element nodes at a global
+  // node without the inverse map; box_N = 0 for any other mesh or storage
+  int box_N, box_ne[3], box_per[3];
+  long long box_n[3];
 };
 
 // The column part of one 1D-IMEX leapfrog step (csrc/imex.cu).  Columns of

@@ -5,6 +5,8 @@
 //                   precomputed inverse map (fixed order, no atomics), inverse
 //                   mass matrix, sources, wall condition, the SSP-RK3 stage
 //                   combination and the primitive fields of the new state;
+//                   on CG boxes the element nodes of each global node come
+//                   from the structured numbering instead of the map;
 // and the launch entry points of all kernels (the element kernels are
 // compiled per precision in volume_fp64.cu, volume_fp32.cu, volume_pairs.cu).
 #include "kernels_common.cuh"
@@ -23,6 +25,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
 template <int MODE, typename RT>
 void launch_update_m(const UpdateArgs& a, unsigned nb, int nt, cudaStream_t s) {
   if (a.gvec) update_kernel<MODE, true, RT><<<nb, nt, 0, s>>>(a);
+  else if (a.box_N) update_kernel<MODE, false, RT, true><<<nb, nt, 0, s>>>(a);
   else update_kernel<MODE, false, RT><<<nb, nt, 0, s>>>(a);
 }
 

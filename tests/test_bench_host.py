@@ -14,8 +14,9 @@ import bench  # noqa: E402
 
 
 def test_flop_models():
-    # per-node form: 39 contractions of N+1 FMAs plus 150 pointwise flops
-    assert bench.volume_flops_per_elem_node(4) == 78 * 5 + 150
+    # per-node form: 36 contractions of N+1 FMAs (12 flux components, 3
+    # directions), 45 chain-rule FMAs, 12 flux and 5 weight flops
+    assert bench.volume_flops_per_elem_node(4) == 72 * 5 + 107
     # affine form: 15 contractions plus 65 pointwise flops
     assert bench.volume_flops_per_elem_node(4, affine=True) == 30 * 5 + 65
     assert bench.volume_flops_per_elem_node(1, affine=True) < bench.volume_flops_per_elem_node(1)
