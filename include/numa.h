@@ -244,6 +244,25 @@ typedef enum { NUMA_RK_SSP3 = 0, NUMA_RK_LS54 = 1, NUMA_LEAPFROG_IMEX = 2 } numa
  * (numa_last_error says why).  Takes effect at the next step. */
 int numa_set_time_scheme(numa_ctx* ctx, int scheme);
 
+/* Slab pipeline of the explicit RK step (SSP-RK3 and LS54) on boxes with CG
+ * storage and walls at the bottom and top.  The elements are cut into
+ * `nslabs` slabs along z and the global nodes into the matching slabs; within
+ * a step the DSS/update of node slab k runs on a second, library-owned stream
+ * beside the element kernel of slab k + 1 (the element kernel is bound by
+ * memory or FP64 work, the update by FP64 work and latency), ordered by
+ * events so that every node is computed exactly as without slabs: results are
+ * identical bit for bit.  nslabs = 0 (the default) chooses 4 slabs for
+ * FP32-mixed meshes of 2^18 or more global nodes (in FP64 and the pairs mode
+ * both kernels compete for the same pipes and the pipeline measured no gain,
+ * so it stays off there); 1 turns the pipeline off; at most 16.  Where a
+ * mesh cannot be cut (shells, DG storage, periodic in z, slabs thinner than
+ * two node planes, planes of fewer than 256 nodes) one slab is used.  *used
+ * (may be NULL) receives the slabs in effect (before numa_bind: those that
+ * numa_bind will use).  numa_time_kernels always runs unpipelined.  The
+ * pipeline creates one CUDA stream and events per context at numa_bind (no
+ * device memory).  NUMA_EINVAL for nslabs outside [0, 16]. */
+int numa_set_slabs(numa_ctx* ctx, int nslabs, int* used);
+
 /* Robert-Asselin filter strength nu of NUMA_LEAPFROG_IMEX, 0 <= nu < 0.5
  * (default 0.05; 0 turns it off).  NUMA_EINVAL outside that range. */
 int numa_set_robert_asselin(numa_ctx* ctx, double nu);

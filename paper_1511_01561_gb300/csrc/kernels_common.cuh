@@ -928,7 +928,7 @@ template <int N, typename T, bool AFF>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     volume_kernel(VolumeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  element_rhs<N, T, AFF>(a, blockIdx.x, smem_raw);
+  element_rhs<N, T, AFF>(a, a.ebeg + (long long)blockIdx.x, smem_raw);
 }
 
 template <typename RT>
@@ -1177,11 +1177,11 @@ __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
 template <int MODE, bool SHELL, typename RT, bool BOX = false>
 __global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
   __shared__ double sums[5][kDssBlock];
-  const long long base = (long long)blockIdx.x * kDssBlock;
+  const long long base = a.ibeg + (long long)blockIdx.x * kDssBlock;
   {
     const int lt = a.order[base + threadIdx.x];
     const long long IA = base + lt;
-    if (IA < a.Ng) {
+    if (IA < a.iend) {
       double s[5];
       if constexpr (BOX) dss_box<RT>(a, IA, s);
       else dss_node<RT>(a, IA, s);
@@ -1192,7 +1192,7 @@ __global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
   __syncthreads();
   const int t = threadIdx.x;
   const long long I = base + t;
-  if (I < a.Ng) update_node_sums<MODE, SHELL>(a, I, sums[0][t], sums[1][t], sums[2][t], sums[3][t], sums[4][t]);
+  if (I < a.iend) update_node_sums<MODE, SHELL>(a, I, sums[0][t], sums[1][t], sums[2][t], sums[3][t], sums[4][t]);
 }
 
 // ---- ragged multi-member kernels (serving) ---------------------------------
@@ -1293,8 +1293,8 @@ cudaError_t launch_volume_t(const VolumeArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set.set();
   }
-  if (a.Ne == 0) return cudaSuccess;
-  volume_kernel<N, T, AFF><<<a.Ne, NT, smem, s>>>(a);
+  if (a.ecnt <= 0) return cudaSuccess;
+  volume_kernel<N, T, AFF><<<a.ecnt, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -70,6 +70,8 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
+  a.ebeg = 0;
+  a.ecnt = a.Ne;
   a.affine = affine_elements(c->cfg) ? (c->rect ? 2 : 1) : 0;
   return a;
 }
@@ -90,6 +92,8 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   a.out = out;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
+  a.ibeg = 0;
+  a.iend = a.Ng;
   a.g = c->cfg.g;
   a.two_omega = 2.0 * c->cfg.Omega;
   a.a = ra;
@@ -297,23 +301,54 @@ cudaError_t enqueue_rk_step(numa_ctx* c, double dt, cudaStream_t s, cudaEvent_t*
   const double* qin[3] = {q, qs, qs};
   double* qout[3] = {qs, qs, q};
   const int ns = rk_stages(c);
+  auto stage_update = [&](int st) {
+    UpdateArgs ua;
+    if (ls) {
+      ua = update_args(c, c->L.re, q, q, q, 4, kLsA[st], kLsB[st], dt);
+      ua.first_stage = st == 0 ? 1 : 0;
+      ua.dq = qs;
+    } else {
+      ua = update_args(c, c->L.re, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt);
+    }
+    return ua;
+  };
+  const SlabPlan& P = c->slabs;
+  if (!ev && P.S > 1) {
+    // slab pipeline: element slabs on s, node slabs on the side stream; the
+    // update of node slab k needs the residuals of element slabs <= k, the
+    // next stage's element slab k the new state of node slabs k and k + 1
+    // (every node's arithmetic is unchanged: the result is the same bit for bit)
+    const int S = P.S;
+    cudaStream_t side = c->side;
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
+    for (int st = 0; st < ns && e == cudaSuccess; ++st) {
+      const double* qi = ls ? q : qin[st];
+      for (int k = 0; k < S && e == cudaSuccess; ++k) {
+        if (st > 0) e = cudaStreamWaitEvent(s, c->ev_upd[k + 1 < S ? k + 1 : S - 1], 0);
+        VolumeArgs va = volume_args(c, qi, c->L.prim, c->L.re);
+        va.ebeg = P.ebeg[k];
+        va.ecnt = P.ebeg[k + 1] - P.ebeg[k];
+        if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, va, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_vol[k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_vol[k], 0);
+        UpdateArgs ua = stage_update(st);
+        ua.ibeg = P.ibeg[k];
+        ua.iend = P.ibeg[k + 1];
+        if (e == cudaSuccess) e = launch_update(c->cfg.precision, ua, side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_upd[k], side);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_upd[S - 1], 0);
+    return e;
+  }
   for (int st = 0; st < ns; ++st) {
     const double* qi = ls ? q : qin[st];
     cudaError_t e = ev ? cudaEventRecord(ev[4 * st], s) : cudaSuccess;
     if (e == cudaSuccess) e = launch_volume(c->mesh.N, c->cfg.precision, volume_args(c, qi, c->L.prim, c->L.re), s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 1], s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 2], s);
-    if (e == cudaSuccess) {
-      UpdateArgs ua;
-      if (ls) {
-        ua = update_args(c, c->L.re, q, q, q, 4, kLsA[st], kLsB[st], dt);
-        ua.first_stage = st == 0 ? 1 : 0;
-        ua.dq = qs;
-      } else {
-        ua = update_args(c, c->L.re, qin[st], q, qout[st], 1, kRkA[st], kRkB[st], dt);
-      }
-      e = launch_update(c->cfg.precision, ua, s);
-    }
+    if (e == cudaSuccess) e = launch_update(c->cfg.precision, stage_update(st), s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4 * st + 3], s);
     if (e != cudaSuccess) return e;
   }
@@ -328,6 +363,59 @@ __global__ void __launch_bounds__(256) weight_metric_kernel(double* met, long lo
   const double mjw = -met[9 * Nl + n];
 #pragma unroll
   for (int t = 0; t < 9; ++t) met[t * Nl + n] *= mjw;
+}
+
+// Slabs of a box along z for the pipelined RK step (see SlabPlan).  A plan
+// needs CG storage, walls at the bottom and top (a periodic seam would tie
+// the first node slab to the last element slab), element slabs at least two
+// lattice planes thick and planes of at least kDssBlock nodes, so that node
+// slab k (rounded down to a kDssBlock boundary) only holds nodes of element
+// slabs <= k and the element slab k reads only node slabs k and k + 1.
+// `want` slabs (0: four for FP32-mixed meshes of 2^18 or more global nodes,
+// where the memory-bound element kernel and the FP64-bound update overlap;
+// in FP64 and the pairs mode both kernels need the FP64 pipe, or the FP32
+// pipe beside it, and the pipeline measured no gain, so none by default).
+SlabPlan plan_slabs(const numa_config& c, const HostMesh& m, int want) {
+  SlabPlan P;
+  if (c.mesh_kind != NUMA_MESH_BOX || c.storage != NUMA_STORAGE_CG || c.periodic[2]) return P;
+  int S = want > 0 ? want : (c.precision == NUMA_FP32_MIXED && m.Ng >= (1LL << 18) ? 4 : 1);
+  if (S > kMaxSlabs) S = kMaxSlabs;
+  if (S > c.nez) S = c.nez;
+  if (S <= 1) return P;
+  const long long N = m.N, nx = (long long)c.nex * N + (c.periodic[0] ? 0 : 1);
+  const long long ny = (long long)c.ney * N + (c.periodic[1] ? 0 : 1), plane = nx * ny;
+  if (plane < kDssBlock) return P;
+  std::vector<int> ez(S + 1);
+  for (int k = 0; k <= S; ++k) ez[k] = (int)((long long)k * c.nez / S);
+  for (int k = 0; k < S; ++k)
+    if ((ez[k + 1] - ez[k]) * N < 2) return P;
+  P.ebeg.resize(S + 1);
+  P.ibeg.resize(S + 1);
+  for (int k = 0; k <= S; ++k) {
+    P.ebeg[k] = (int)((long long)ez[k] * c.nex * c.ney);
+    P.ibeg[k] = k == S ? m.Ng : (ez[k] * N * plane) / kDssBlock * kDssBlock;
+  }
+  for (int k = 0; k < S; ++k)
+    if (P.ibeg[k + 1] <= P.ibeg[k] || P.ibeg[k] > ez[k] * N * plane) return SlabPlan();
+  P.S = S;
+  return P;
+}
+
+// The side stream and the events of the slab pipeline (once per context,
+// on the device current at the call).
+cudaError_t ensure_slab_streams(numa_ctx* c) {
+  if (c->side) return cudaSuccess;
+  // the update stream at the highest priority: its blocks take SM slots as
+  // soon as element blocks finish, so that the two kernels share the SMs
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < kMaxSlabs && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&c->ev_vol[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_upd[k], cudaEventDisableTiming);
+  }
+  return e;
 }
 
 // Whether every element has diagonal metric terms (off-diagonal entries
@@ -565,9 +653,14 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind upload");
   c->L = L;
   c->rect = rect;
+  c->slabs = plan_slabs(c->cfg, m, c->nslab_req);
+  if (c->slabs.S > 1) {
+    e = ensure_slab_streams(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind slab stream and events");
+  }
   // kernel attributes are set outside any stream capture
   VolumeArgs probe = volume_args(c, L.q, L.prim, L.re);
-  probe.Ne = 0;
+  probe.ecnt = 0;
   e = launch_volume(m.N, c->cfg.precision, probe, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_bind kernel setup");
   c->stream = s;
@@ -841,6 +934,24 @@ int numa_set_time_scheme(numa_ctx* c, int scheme) {
   return NUMA_OK;
 }
 
+int numa_set_slabs(numa_ctx* c, int nslabs, int* used) {
+  if (!c) return NUMA_EINVAL;
+  if (nslabs < 0 || nslabs > kMaxSlabs) return fail(c, NUMA_EINVAL, "slabs must be in [0, 16]");
+  c->nslab_req = nslabs;
+  const SlabPlan P = plan_slabs(c->cfg, c->mesh, nslabs);
+  if (c->bound && P.S > 1) {
+    cudaError_t e = ensure_slab_streams(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "numa_set_slabs stream and events");
+  }
+  if (c->bound) c->slabs = P;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (used) *used = c->bound ? c->slabs.S : P.S;
+  return NUMA_OK;
+}
+
 int numa_set_robert_asselin(numa_ctx* c, double nu) {
   if (!c) return NUMA_EINVAL;
   if (!(nu >= 0.0 && nu < 0.5)) return fail(c, NUMA_EINVAL, "Robert-Asselin strength must be in [0, 0.5)");
@@ -867,6 +978,12 @@ int numa_destroy(numa_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->fgraph) cudaGraphExecDestroy(c->fgraph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (int k = 0; k < kMaxSlabs; ++k) {
+    if (c->ev_vol[k]) cudaEventDestroy(c->ev_vol[k]);
+    if (c->ev_upd[k]) cudaEventDestroy(c->ev_upd[k]);
+  }
   delete c;
   return NUMA_OK;
 }

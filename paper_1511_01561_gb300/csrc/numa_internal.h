@@ -126,6 +126,7 @@ struct VolumeArgs {
   const double* ww64;  // FP64 rectilinear form: w_i w_j
   long long Ng, Nl;
   int Ne;
+  int ebeg, ecnt;      // the launch covers elements [ebeg, ebeg + ecnt) (a slab, or all: 0, Ne)
   int affine;          // 0: per-node form; 1: every element is affine, the kernel takes the
                        // contravariant-flux form; 2: every element is also rectilinear (diagonal
                        // metric terms), FP64 takes the folded form (volume_element_rect)
@@ -154,6 +155,9 @@ struct UpdateArgs {
                        // write the primitives of out)
   int* flag;           // non-finite flag
   PrimArgs pa;         // primitive output of mode 1 (pa.q unused)
+  // the launch covers global nodes [ibeg, iend): a slab (ibeg a multiple of
+  // kDssBlock), or all: 0, Ng
+  long long ibeg, iend;
   // CG box meshes: the lattice of the structured global numbering (g = ix +
   // nx (iy + ny iz)), from which the DSS finds the element nodes at a global
   // node without the inverse map; box_N = 0 for any other mesh or storage
@@ -273,6 +277,18 @@ cudaError_t launch_update_ragged(int precision, bool shell, int stage, const Mem
 
 }  // namespace numa
 
+namespace numa {
+// Slabs of a box along z for the pipelined RK step: element slab k is
+// elements [ebeg[k], ebeg[k+1]), node slab k global nodes [ibeg[k],
+// ibeg[k+1]) (ibeg a multiple of kDssBlock).  S = 1: no pipeline.
+struct SlabPlan {
+  int S = 1;
+  std::vector<int> ebeg;
+  std::vector<long long> ibeg;
+};
+constexpr int kMaxSlabs = 16;
+}  // namespace numa
+
 // A context: the host mesh of one configuration and, once bound, the layout of
 // its device workspace.
 struct numa_ctx {
@@ -282,6 +298,10 @@ struct numa_ctx {
   bool bound = false;
   bool prim_valid = false;  // L.prim holds the primitive fields of L.q
   bool rect = false;        // FP64, affine and every element rectilinear: the folded element kernel
+  int nslab_req = 0;        // slabs asked for by numa_set_slabs (0: automatic)
+  numa::SlabPlan slabs;     // the plan in use (made at bind and by numa_set_slabs)
+  cudaStream_t side = nullptr;  // the second stream of the slab pipeline
+  cudaEvent_t ev_fork = nullptr, ev_vol[numa::kMaxSlabs] = {}, ev_upd[numa::kMaxSlabs] = {};
   cudaStream_t stream = nullptr;
   std::string err;
   double gamma = 1.4;

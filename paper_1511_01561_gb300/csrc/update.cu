@@ -45,9 +45,10 @@ cudaError_t launch_volume(int N, int precision, const VolumeArgs& a, cudaStream_
 }
 
 cudaError_t launch_update(int precision, const UpdateArgs& a, cudaStream_t s) {
-  if (a.Ng == 0) return cudaSuccess;
+  if (a.iend <= a.ibeg) return cudaSuccess;
+  if (a.ibeg % kDssBlock) return cudaErrorInvalidValue;
   const int nt = kDssBlock;  // the kernel's block size: one block per DSS-order block
-  const unsigned nb = (unsigned)((a.Ng + nt - 1) / nt);
+  const unsigned nb = (unsigned)((a.iend - a.ibeg + nt - 1) / nt);
   const bool f32 = precision == NUMA_FP32_MIXED;
   if (a.mode == 0) {
     if (f32) launch_update_m<0, float>(a, nb, nt, s);

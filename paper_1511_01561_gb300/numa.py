@@ -71,6 +71,7 @@ def _load():
         "numa_set_filter": [vp, i, i, d, d],
         "numa_set_time_scheme": [vp, i],
         "numa_set_robert_asselin": [vp, d],
+        "numa_set_slabs": [vp, i, ctypes.POINTER(i)],
         "numa_filter": [vp],
         "numa_check_finite": [vp, ctypes.POINTER(i)],
         "numa_time_kernels": [vp, d, i, dp, dp],
@@ -193,6 +194,14 @@ def numa_set_time_scheme(ctx, scheme: str) -> None:
 
 def numa_set_robert_asselin(ctx, nu: float) -> None:
     _check(ctx, lib.numa_set_robert_asselin(ctx, nu))
+
+
+def numa_set_slabs(ctx, nslabs: int) -> int:
+    """Slabs of the pipelined RK step (0: automatic, 1: off); returns the
+    slabs in effect."""
+    used = ctypes.c_int()
+    _check(ctx, lib.numa_set_slabs(ctx, int(nslabs), ctypes.byref(used)))
+    return used.value
 
 
 def numa_set_filter(ctx, every: int, s: int, p: float, mu: float = 1.0) -> None:
@@ -325,6 +334,10 @@ class Solver:
     def set_robert_asselin(self, nu: float):
         """Robert-Asselin filter strength of the "imex" scheme (default 0.05)."""
         numa_set_robert_asselin(self.ctx, nu)
+
+    def set_slabs(self, nslabs: int) -> int:
+        """Slabs of the pipelined RK step on boxes (0: automatic, 1: off)."""
+        return numa_set_slabs(self.ctx, nslabs)
 
     def set_filter(self, every: int, s: int, p: float, mu: float = 1.0):
         """Boyd-Vandeven filter after every `every`-th step (0: off)."""

@@ -114,3 +114,27 @@ def test_argument_errors_without_gpu(numa):
         numa.numa_destroy(ctx)
     assert numa.lib.numa_destroy(None) == -1
     assert numa.lib.numa_rhs(None, None, None) == -1
+
+
+@pytest.mark.parametrize("cfg,want,expect", [
+    (dict(I.box(32, 4), precision="fp32_mixed"), 0, 4),  # FP32-mixed, 2.1M nodes: four by default
+    (I.box(32, 4), 0, 1),                       # FP64: none by default
+    (I.box((4, 4, 8), 4), 0, 1),                # small mesh: none by default
+    (I.box((4, 4, 8), 4), 4, 4),
+    (I.box((4, 4, 8), 4), 16, 8),               # at most one slab per element layer
+    (I.box((4, 4, 8), 1), 4, 1),                # slabs thinner than two node planes
+    (I.box((4, 4, 8), 4, periodic=(0, 0, 1)), 4, 1),  # periodic seam in z
+    (I.box((2, 2, 8), 4), 4, 1),                # planes of fewer than 256 nodes
+    (I.shell(2, 2, 3), 4, 1),
+    (dict(I.box((4, 4, 8), 4), storage="dg"), 4, 1),
+])
+def test_slab_plan(numa, cfg, want, expect):
+    """numa_set_slabs before numa_bind reports the slabs the bind will use
+    (host logic only: no GPU call)."""
+    ctx = numa.numa_create(cfg)
+    try:
+        assert numa.numa_set_slabs(ctx, want) == expect
+        with pytest.raises(numa.NumaError):
+            numa.numa_set_slabs(ctx, 17)
+    finally:
+        numa.numa_destroy(ctx)
