@@ -45,9 +45,9 @@ __device__ __forceinline__ void dz_row_range(int k, int N, int nz, int& j0, int&
   }
 }
 
-// RADIAL = false: z-columns of the box (node c + ncol k, W = U_z);
-// RADIAL = true: radial columns of the shell (node cols[k ncol + c],
-// W = U . r_hat, U^{n+1} = U* + (x_W - W*) r_hat).
+// Column c, level k is global node c + ncol k.  RADIAL = false: z-columns of
+// the box (W = U_z); RADIAL = true: radial columns of the shell (W = U . r_hat,
+// U^{n+1} = U* + (x_W - W*) r_hat).
 template <bool RADIAL>
 __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   extern __shared__ __align__(16) double sm[];
@@ -67,10 +67,7 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
   const long long col0 = (long long)blockIdx.x * CPB;
   const double nu = a.nu, tau = a.tau;
   const int items = nz * CPB;
-  auto node = [&](long long col, int k) -> long long {
-    if constexpr (RADIAL) return a.cols[col + ncol * k];
-    else return col + ncol * k;
-  };
+  auto node = [&](long long col, int k) -> long long { return col + ncol * k; };
 
   // explicit step, the filter's first part; U and V finished in the box,
   // U* parked in q on the shell
@@ -244,8 +241,7 @@ cudaError_t launch_imex(const ImexArgs& a, cudaStream_t s) {
   if (smem > kImexSmemMax || !imex_attr.has()) return cudaErrorInvalidValue;
   if (a.ncol == 0) return cudaSuccess;
   const long long blocks = (a.ncol + a.cols_per_block - 1) / a.cols_per_block;
-  if ((a.cols != nullptr) != (a.nrm != nullptr)) return cudaErrorInvalidValue;
-  if (a.cols) imex_column_kernel<true><<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
+  if (a.nrm) imex_column_kernel<true><<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
   else imex_column_kernel<false><<<(unsigned)blocks, kImexThreads, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -49,53 +49,33 @@ size_t imex_table_doubles(int nz, int N) {
 
 namespace {
 
-// Radial columns of the shell: walk the element columns (layers are the
-// fastest element index) and record, per surface point, its global node at
-// every level; stored [level][column], so that a warp reading one level of
-// consecutive columns reads consecutive entries.
-bool shell_columns(const numa_config& c, const HostMesh& m, long long ncol, int nz, std::vector<int32_t>& cols,
-                   std::string& err) {
+// Radial columns of the shell: the mesh numbers global nodes level by level
+// (node = column + ncol * level, level = il N + k from the bottom), so a
+// radial column is the same stride-ncol sequence as a z-column of the box.
+// Check that structure: walk the element columns (layers are the fastest
+// element index) and require every node of the column above bottom node c
+// to be c + ncol * level.
+bool check_shell_columns(const numa_config& c, const HostMesh& m, long long ncol, int nz, std::string& err) {
   const int N = m.N, P = m.P, nl = c.nlayer;
   const long long ecols = m.Ne / nl;
-  cols.assign((size_t)ncol * nz, -1);
-  std::vector<int32_t> col_of((size_t)m.Ng, -1);
-  long long next = 0;
   for (long long ec = 0; ec < ecols; ++ec)
     for (int j = 0; j < P; ++j)
       for (int i = 0; i < P; ++i) {
-        const int32_t bottom = m.l2g[(ec * nl) * m.Np + i + P * j];
-        int32_t col = col_of[bottom];
-        const bool fresh = col < 0;
-        if (fresh) {
-          if (next >= ncol) {
-            err = "1D-IMEX: more radial columns than surface points";
-            return false;
-          }
-          col = (int32_t)next++;
-          col_of[bottom] = col;
+        const long long col = m.l2g[(ec * nl) * m.Np + i + P * j];
+        if (col < 0 || col >= ncol) {
+          err = "1D-IMEX: a bottom node is not on level 0";
+          return false;
         }
         for (int il = 0; il < nl; ++il)
-          for (int k = (il == 0 ? 0 : 1); k < P; ++k) {
-            const int32_t g = m.l2g[(ec * nl + il) * m.Np + i + P * (j + P * k)];
-            int32_t& slot = cols[(size_t)(il * N + k) * ncol + col];
-            if (fresh) slot = g;
-            else if (slot != g) {
-              err = "1D-IMEX: inconsistent radial column";
+          for (int k = 0; k < P; ++k)
+            if (m.l2g[(ec * nl + il) * m.Np + i + P * (j + P * k)] != col + ncol * (il * N + k)) {
+              err = "1D-IMEX: radial columns are not numbered level by level";
               return false;
             }
-          }
       }
-  if (next != ncol) {
-    err = "1D-IMEX: radial columns do not cover the surface";
+  if ((long long)nz * ncol != m.Ng) {
+    err = "1D-IMEX: radial columns do not cover the nodes";
     return false;
-  }
-  std::vector<char> seen((size_t)m.Ng, 0);
-  for (int32_t g : cols) {
-    if (g < 0 || g >= m.Ng || seen[g]) {
-      err = "1D-IMEX: radial columns do not partition the nodes";
-      return false;
-    }
-    seen[g] = 1;
   }
   return true;
 }
@@ -113,11 +93,8 @@ bool imex_operator(const numa_config& c, const HostMesh& m, ImexTables& t, std::
     return false;
   }
   const bool shell = c.mesh_kind == NUMA_MESH_SHELL;
-  t.cols.clear();
-  if (shell && !shell_columns(c, m, ncol, nz, t.cols, err)) return false;
-  auto node = [&](long long col, int k) -> long long {
-    return shell ? t.cols[(size_t)k * ncol + col] : col + (long long)k * ncol;
-  };
+  if (shell && !check_shell_columns(c, m, ncol, nz, err)) return false;
+  auto node = [&](long long col, int k) -> long long { return col + (long long)k * ncol; };
   // the reference state must be the same in every column (it depends on the height only)
   for (int v = 0; v < 3; ++v)
     for (int k = 0; k < nz; ++k) {

@@ -140,9 +140,13 @@ void box_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
 
 // Cubed-sphere shell: element e = il + nl (ia + np (ib + np p)) so that each
 // radial column is contiguous, bottom to top (Sec. 4, p6est layers).  A
-// surface node is identified exactly by its integer point on the cube
+// surface point is identified exactly by its integer point on the cube
 // lattice K e_n + (2 ta - K) e_a + (2 tb - K) e_b (K = np N), which is the
-// same from every panel that shares it; global ids follow first appearance.
+// same from every panel that shares it.  Global nodes are numbered level by
+// level: node = column + ncol * level, with the ncol surface points (radial
+// columns) numbered by first appearance in element-node order and
+// level = il N + k from the bottom, so that a radial column is the same
+// stride-ncol sequence as a z-column of the box.
 void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
   const int N = m.N, P = m.P, np = c.npanel, nl = c.nlayer;
   const long long K = (long long)np * N, W = 2 * K + 1, NR = (long long)nl * N + 1;
@@ -151,6 +155,7 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
   X.assign(3 * m.Nl, 0.0);
   m.hgt.assign(m.Nl, 0.0);
   std::vector<long long> key(m.Nl);
+  std::vector<int> level(m.Nl);
   const double dA = 0.5 * kPi / np, dR = (c.r_outer - c.r_inner) / nl;
   for (int p = 0; p < 6; ++p)
     for (int ib = 0; ib < np; ++ib)
@@ -177,38 +182,32 @@ void shell_nodes(const numa_config& c, HostMesh& m, std::vector<double>& X) {
                 long long L[3];
                 for (int d = 0; d < 3; ++d)
                   L[d] = K * kFrame[p][2][d] + (2 * la - K) * kFrame[p][0][d] + (2 * lb - K) * kFrame[p][1][d];
-                long long skey = ((L[0] + K) * W + (L[1] + K)) * W + (L[2] + K);
-                key[n] = skey * NR + ((long long)il * N + k);
+                key[n] = ((L[0] + K) * W + (L[1] + K)) * W + (L[2] + K);  // the surface point
+                level[n] = (int)((long long)il * N + k);
               }
         }
-  // first-appearance numbering of unique keys
+  // columns: the unique surface points, numbered by first appearance
   std::vector<long long> order(m.Nl);
   std::iota(order.begin(), order.end(), 0LL);
   std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return key[a] < key[b]; });
-  std::vector<long long> first(m.Nl, -1);  // per element node: first node with its key
-  long long u = 0;
+  std::vector<long long> first(m.Nl, -1);  // per element node: first node with its surface point
   std::vector<long long> firsts;
   for (long long t = 0; t < m.Nl; ++t) {
-    if (t == 0 || key[order[t]] != key[order[t - 1]]) {
-      firsts.push_back(order[t]);
-      ++u;
-    }
+    if (t == 0 || key[order[t]] != key[order[t - 1]]) firsts.push_back(order[t]);
     first[order[t]] = firsts.back();
   }
   std::vector<long long> f_sorted = firsts;
   std::sort(f_sorted.begin(), f_sorted.end());
-  std::vector<int32_t> id_of_first(m.Nl, -1);
-  for (size_t t = 0; t < f_sorted.size(); ++t) id_of_first[f_sorted[t]] = (int32_t)t;
-  m.Ng = u;
+  std::vector<int32_t> col_of_first(m.Nl, -1);
+  for (size_t t = 0; t < f_sorted.size(); ++t) col_of_first[f_sorted[t]] = (int32_t)t;
+  const long long ncol = (long long)f_sorted.size();
+  m.Ng = ncol * NR;
   m.l2g.assign(m.Nl, 0);
-  for (long long n = 0; n < m.Nl; ++n) m.l2g[n] = id_of_first[first[n]];
+  for (long long n = 0; n < m.Nl; ++n) m.l2g[n] = (int32_t)(col_of_first[first[n]] + ncol * level[n]);
   m.wall.assign(m.Ng, 0);
-  for (long long e = 0; e < m.Ne; ++e) {
-    int il = (int)(e % nl);
-    for (int l = 0; l < m.Np; ++l) {
-      int k = l / (P * P);
-      if ((il == 0 && k == 0) || (il == nl - 1 && k == N)) m.wall[m.l2g[e * m.Np + l]] = 8;
-    }
+  for (long long c = 0; c < ncol; ++c) {  // the bottom and the lid
+    m.wall[c] = 8;
+    m.wall[c + ncol * (NR - 1)] = 8;
   }
 }
 

@@ -217,9 +217,6 @@ int imex_prepare(numa_ctx* c, double dt) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.th0, t.th0.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.gl, t.gl.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.r2, t.r2.data(), nz * 8, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess && !t.cols.empty())
-    e = cudaMemcpyAsync(c->L.imex_cols, t.cols.data(), t.cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                        c->stream);
   int ku[2] = {0, 0};
   for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
     if (!imex_factor(t, f == 0 ? dt : 0.5 * dt, Lf, Uf, piv, &ku[f], err)) return fail(c, NUMA_EINVAL, err);
@@ -264,7 +261,6 @@ cudaError_t enqueue_imex_step(numa_ctx* c, double dt, bool start, cudaStream_t s
     a.gl = p.gl;
     a.r2 = p.r2;
     const bool shell = c->cfg.mesh_kind == NUMA_MESH_SHELL;
-    a.cols = shell ? c->L.imex_cols : nullptr;
     a.nrm = shell ? c->L.nrm : nullptr;
     a.Lf = p.Lf[f];
     a.Uf = p.Uf[f];
@@ -482,7 +478,6 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   if (imex_supported(c, &ncol, &nz, nullptr)) {
     d.imex = (double*)take(imex_table_doubles(nz, c.N) * 8);
     d.imex_piv = (int*)take(6 * (size_t)nz * sizeof(int));
-    if (c.mesh_kind == NUMA_MESH_SHELL) d.imex_cols = (int32_t*)take((size_t)ncol * nz * sizeof(int32_t));
   }
   d.bytes = off;
   if (L) *L = d;

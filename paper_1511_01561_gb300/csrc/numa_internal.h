@@ -84,7 +84,6 @@ struct DevLayout {
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
   double* imex = nullptr;    // 1D-IMEX tables (imex_table_doubles), boxes with walled columns only
   int* imex_piv = nullptr;   // [2][nz][3] pivots and row extents of the two factorisations (dt, dt/2)
-  int32_t* imex_cols = nullptr;  // shell: [nz][ncol] global nodes of the radial columns
   int* flags = nullptr;      // [64]: 0 = non-finite
   size_t bytes = 0;
 };
@@ -165,9 +164,9 @@ struct UpdateArgs {
   long long box_n[3];
 };
 
-// The column part of one 1D-IMEX leapfrog step (csrc/imex.cu).  Columns of
-// a walled box: column c, level k is global node c + ncol k; radial columns
-// of the shell: global node cols[k ncol + c], W = U . r_hat.  The kernel
+// The column part of one 1D-IMEX leapfrog step (csrc/imex.cu).  Column c,
+// level k is global node c + ncol k: the z-columns of a walled box, or the
+// radial columns of the shell (numbered level by level), W = U . r_hat.  The kernel
 // forms q* = qprev + cR R, applies the implicit vertical correction with the
 // banded LU factors of the Schur matrix, writes q^{n+1} into q, the
 // Robert-Asselin filtered q^n into qs and the primitive fields of q^{n+1}.
@@ -181,8 +180,7 @@ struct ImexArgs {
   const double* th0;    // [nz] Theta0 / rho0
   const double* gl;     // [nz] gravity g(r) at each level (the box: g)
   const double* r2;     // [nz] 2 / r at each level, the spherical divergence term (the box: 0)
-  const int32_t* cols;  // shell: [nz][ncol] global node of each radial column at each level; box: null
-  const double* nrm;    // shell: r_hat [3][Ng]; box: null
+  const double* nrm;    // shell: r_hat [3][Ng] (radial columns); box: null
   const double* Lf;     // [nz][kl]: multipliers of elimination step k (rows k+1 .. k+kl)
   const double* Uf;     // [nz][1 + ku]: 1 / U_kk, then U_{k,k+1} .. U_{k,k+ku}
   const int* piv;       // [nz][3]: row swapped with row k at step k, multipliers used (last
@@ -199,7 +197,6 @@ struct ImexTables {
   int nz = 0, N = 0, kl = 0, ku = 0;
   std::vector<double> Dz, c2, th0;  // [nz][2N+1], [nz], [nz]
   std::vector<double> gl, r2;       // [nz] g(r) and 2 / r per level (box: g and 0)
-  std::vector<int32_t> cols;        // shell: [nz][ncol] global nodes of the radial columns
   std::vector<double> Lf, Uf;       // [nz][kl], [nz][1 + 4N] (ku <= 4N used)
   std::vector<int> piv;             // [nz][3] (see ImexArgs::piv)
 };
