@@ -84,12 +84,8 @@ FP64_PEAK_SOURCE = "nominal FP64 FMA rate; measured 1.258 TFLOP/s (profiles/p0_a
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "0b34af9fc5ddb0c2", "workload": "bubble_32x32x32_N4",
-               "volume_fp64_affine": 224.309504e6 + 125.987072e6,
-               "volume_fp64_nodal": 482.401024e6 + 142.800128e6,
-               "volume_fp32_affine": 139.232768e6 + 49.504512e6,
-               "volume_fp32_nodal": 249.009152e6 + 60.783872e6,
-               "volume_pairs_affine": 224.342272e6 + 129.383168e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "064348dba0313bc0", "workload": "bubble_32x32x32_N4",
+               "volume_fp64_affine": 154.685696e6 + 120.789504e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
