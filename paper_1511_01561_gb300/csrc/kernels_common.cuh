@@ -149,18 +149,24 @@ __device__ __forceinline__ Pairs pp_sub(Pairs a, Pairs b) {
 __device__ __noinline__ double eos_ratio_rare(double x, double gamma) { return expm1(gamma * log1p(x)); }
 
 // (1+x)^gamma - 1 with full relative accuracy: the binomial series
-// sum_k C(gamma,k) x^k (Horner), 6 terms for |x| <= 2^-10 and 12 terms for
-// |x| <= 2^-5 (truncation below 1e-17 relative in both), else
-// expm1(gamma log1p(x)).  The term count is a loop bound, not a branch, so
-// that the two series are never both issued.
+// sum_k C(gamma,k) x^k (Horner) for |x| <= 2^-5, else expm1(gamma log1p(x)).
+// For 1 < gamma < 2 every |C(gamma,k+1) / C(gamma,1)| <= 1, so the relative
+// truncation after K terms is below |x|^K; K is the least count that keeps
+// it below 2^-60 (2^-30 for a result stored as a float, F32OUT): 2, 3, 4, 5,
+// 6 or 12 terms for |x| <= 2^-30, 2^-20, 2^-15, 2^-12, 2^-10, 2^-5 (F32OUT:
+// 1, 2, 3, 6 for 2^-30, 2^-15, 2^-10, 2^-5).  The term count is a loop bound,
+// not a branch, so a warp runs the series once, to its largest count.
 template <bool F32OUT = false>
 __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
   const unsigned hx = ((unsigned)__double2hiint(x)) & 0x7fffffffu;  // |x| by its high word
   if (hx > 0x3fa00000u) return eos_ratio_rare(x, a.gamma);          // |x| > 2^-5
-  // relative truncation about |x|^K: below 2^-53 with 6 (|x| <= 2^-10) or 12
-  // (|x| <= 2^-5) terms; for a result stored as a float (F32OUT), below 2^-26
-  // with 3 or 6 terms
-  const int K = hx <= 0x3f500000u ? (F32OUT ? 3 : 6) : (F32OUT ? 6 : kEosTerms);
+  // thresholds 2^-e as high words: (1023 - e) << 20
+  int K;
+  if constexpr (F32OUT)
+    K = hx <= 0x3e100000u ? 1 : hx <= 0x3f000000u ? 2 : hx <= 0x3f500000u ? 3 : 6;
+  else
+    K = hx <= 0x3e100000u ? 2 : hx <= 0x3eb00000u ? 3 : hx <= 0x3f000000u ? 4 : hx <= 0x3f300000u ? 5
+      : hx <= 0x3f500000u ? 6 : kEosTerms;
   double t = a.eos[K - 1];
   for (int k = K - 2; k >= 0; --k) t = fma(t, x, a.eos[k]);
   return t * x;
@@ -924,8 +930,17 @@ __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, un
   }
 }
 
+// Resident CTAs per SM asked of the compiler: the FP32 line kernel is bound
+// by the latency of its gathers, so at N = 4 it is held to 32 registers (16
+// CTAs of 128 threads per SM) in the affine form and 40 (12 CTAs) in the
+// per-node form; the others take the compiler's choice.
 template <int N, typename T, bool AFF>
-__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+constexpr int volume_min_blocks() {
+  return std::is_same<T, float>::value && N == 4 ? (AFF ? 16 : 12) : 1;
+}
+
+template <int N, typename T, bool AFF>
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32, (volume_min_blocks<N, T, AFF>()))
     volume_kernel(VolumeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   element_rhs<N, T, AFF>(a, a.ebeg + (long long)blockIdx.x, smem_raw);

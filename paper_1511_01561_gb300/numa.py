@@ -354,6 +354,65 @@ class Solver:
         return numa_check_finite(self.ctx)
 
 
+class HostStepper:
+    """Steps from host memory to host memory, pipelined: each submit() copies
+    a state from pinned host memory to the device, advances it by nsteps
+    steps of the solver's integrator, and copies the result back to pinned
+    host memory.  The host-to-device copy of the next state and the
+    device-to-host copy of the previous result run on two copy streams of
+    their own while the solver's stream computes, so that consecutive
+    submits overlap their copies with each other's steps.  Two device
+    staging buffers per direction alternate between submits.  synchronize()
+    waits until every result has landed; an output buffer may be read only
+    after it.  The states go through numa_set_state / numa_get_state
+    (device to device) and the steps through numa_rk_step."""
+
+    def __init__(self, solver: "Solver"):
+        t = solver.torch
+        self.s = solver
+        self.t = t
+        dev = solver.device
+        self.h2d = t.cuda.Stream(dev)
+        self.d2h = t.cuda.Stream(dev)
+        shape = (5, solver.Ng)
+        self.din = [t.empty(shape, dtype=t.float64, device=dev) for _ in range(2)]
+        self.dout = [t.empty(shape, dtype=t.float64, device=dev) for _ in range(2)]
+        ev = lambda: t.cuda.Event()  # noqa: E731
+        self.in_ready, self.in_used = [ev(), ev()], [ev(), ev()]
+        self.out_ready, self.out_done = [ev(), ev()], [ev(), ev()]
+        for e in self.in_used + self.out_done:
+            e.record(solver.stream)
+        self.k = 0
+
+    def submit(self, q_host, out_host, dt: float, nsteps: int = 1):
+        t, main, i = self.t, self.s.stream, self.k % 2
+        ctx = self.s.ctx
+        # host -> device staging i, once the step that read it last has copied it in
+        self.h2d.wait_event(self.in_used[i])
+        with t.cuda.stream(self.h2d):
+            self.din[i].copy_(q_host, non_blocking=True)
+        self.in_ready[i].record(self.h2d)
+        main.wait_event(self.in_ready[i])
+        numa_set_state(ctx, self.din[i].data_ptr(), True)
+        self.in_used[i].record(main)
+        for _ in range(nsteps):
+            numa_rk_step(ctx, dt)
+        # result -> device staging i (free once its previous copy out is done) -> host
+        main.wait_event(self.out_done[i])
+        numa_get_state(ctx, self.dout[i].data_ptr(), True)
+        self.out_ready[i].record(main)
+        self.d2h.wait_event(self.out_ready[i])
+        with t.cuda.stream(self.d2h):
+            out_host.copy_(self.dout[i], non_blocking=True)
+        self.out_done[i].record(self.d2h)
+        self.k += 1
+
+    def synchronize(self):
+        self.s.stream.synchronize()
+        self.h2d.synchronize()
+        self.d2h.synchronize()
+
+
 # ---- serving: continuous batching over one device arena --------------------
 
 REQ_STATUS = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
