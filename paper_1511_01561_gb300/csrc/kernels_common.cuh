@@ -930,17 +930,8 @@ __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, un
   }
 }
 
-// Resident CTAs per SM asked of the compiler: the FP32 line kernel is bound
-// by the latency of its gathers, so at N = 4 it is held to 32 registers (16
-// CTAs of 128 threads per SM) in the affine form and 40 (12 CTAs) in the
-// per-node form; the others take the compiler's choice.
 template <int N, typename T, bool AFF>
-constexpr int volume_min_blocks() {
-  return std::is_same<T, float>::value && N == 4 ? (AFF ? 16 : 12) : 1;
-}
-
-template <int N, typename T, bool AFF>
-__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32, (volume_min_blocks<N, T, AFF>()))
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     volume_kernel(VolumeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   element_rhs<N, T, AFF>(a, a.ebeg + (long long)blockIdx.x, smem_raw);
