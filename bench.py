@@ -56,6 +56,8 @@ def parse_args(argv=None):
                    help="rate of a second Poisson stream / saturated request rate (0 skips it)")
     p.add_argument("--no-shell", action="store_true", help="skip the cubed-sphere shell block")
     p.add_argument("--no-serve-block", action="store_true", help="skip the reduced serving block")
+    p.add_argument("--no-precision", action="store_true",
+                   help="skip the FP32-mixed / FP64-pairs difference from the FP64 state")
     p.add_argument("--serve-block-requests", type=int, default=16)
     p.add_argument("--serve-block-steps-scale", type=float, default=0.1)
     p.add_argument("--peaks", action="store_true",
@@ -332,6 +334,8 @@ def run_mine(args):
             dist.destroy_process_group()
         return
 
+    snaps = {} if not args.no_precision else None
+
     def measure(precision, form="auto", scheme="ssp3", storage="cg", wl=None):
         wl = w if wl is None else wl
         s = numa.Solver(dict(wl["cfg"], metric_form=form, storage=storage), precision, device=str(dev))
@@ -351,6 +355,10 @@ def run_mine(args):
         barrier()
         ms = max_ranks(e0.elapsed_time(e1))
         ck = clocks.stop() if clocks else None
+        if snaps is not None and storage == "cg" and scheme == "ssp3" and form == "auto":
+            # the state after warm-up + timed steps, for the precision-form comparison
+            snaps[(precision, wl["cfg"]["kind"])] = s.get_state(
+                torch.empty((5, s.Ng), dtype=torch.float64, device=dev))
         # per-kernel device times over the same number of steps (event-bracketed launches)
         ms_vol, ms_upd = s.time_kernels(wl["dt"], args.steps)
         info = s.info
@@ -540,6 +548,9 @@ def run_mine(args):
                 sh[prec]["speedup_vs_fp64"] = sh[prec]["value"] / sh["fp64"]["value"]
                 sh[prec]["volume_hbm_frac"] = b32 / (vols * 1e-3 / nl) / 1e9 / hbm_gbs
         line["shell"] = sh
+    if snaps:
+        line["precision_forms"] = precision_block(snaps, args)
+        snaps.clear()
     if not args.no_serve_block and world == 1:
         line["serving"] = serving_block(args, numa, torch)
     if cpu is not None:
@@ -548,6 +559,35 @@ def run_mine(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def precision_block(snaps, args):
+    """Difference of the FP32-mixed and FP64-pairs states from the FP64 state
+    after the same warm-up + timed SSP-RK3 steps from the same initial state:
+    per variable, relative L2 and Linf (||a - b|| / ||b||, b the FP64 state).
+    The FP64 path itself is held to the oracle by the parity tests; this is
+    the precision forms' drift from it on the bench workloads."""
+    vars_ = ["rho'", "U_x", "U_y", "U_z", "Theta'"]
+    out = {"what": "relative L2 / Linf difference from the FP64 state after the same steps, per variable",
+           "steps": args.warmup + args.steps}
+    for kind in ("box", "shell"):
+        ref = snaps.get(("fp64", kind))
+        if ref is None:
+            continue
+        blk = {}
+        for prec in ("fp32_mixed", "fp64_pairs"):
+            a = snaps.get((prec, kind))
+            if a is None:
+                continue
+            d = (a - ref)
+            res = {}
+            for v, name in enumerate(vars_):
+                n2, ni = float(ref[v].norm()), float(ref[v].abs().max())
+                res[name] = [float(d[v].norm()) / n2 if n2 > 0 else None,
+                             float(d[v].abs().max()) / ni if ni > 0 else None]
+            blk[prec] = res
+        out[kind] = blk
+    return out
 
 
 def imex_block(args, numa, torch, dev, barrier, max_ranks):

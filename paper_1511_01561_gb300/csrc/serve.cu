@@ -38,6 +38,12 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kMaxGroups = 16;
 constexpr size_t kMaxInflight = 3;
+// Captured streams of one serving step: groups run as independent branches
+// of the step graph (round-robin over this many streams, the capture stream
+// included), so that one group's kernels fill the SMs another leaves idle
+// (the tail of a persistent launch, a small group, an FP64-pipe-bound group
+// beside a memory-bound one).
+constexpr int kBranches = 4;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -136,6 +142,9 @@ struct numa_sched {
   cudaStream_t stream = nullptr;  // compute stream (caller's)
   cudaStream_t upload = nullptr;  // geometry uploads of newly admitted members
   cudaStream_t cap = nullptr;
+  cudaStream_t branch[kBranches] = {};  // [0] unused: branch 0 is the capture stream
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kBranches] = {};
   // device tables (at the start of the arena) and their pinned host mirrors
   MemberDesc* d_desc = nullptr;
   RaggedGroup* d_groups = nullptr;
@@ -247,20 +256,41 @@ void rebuild_tables(numa_sched* s) {
 
 // One RK step of every group: 3 stages x (ragged volume, ragged update), each
 // stage reading its own copy of the member table (the volume kernel's input
-// state differs between the first and the later stages).
-cudaError_t enqueue_step(numa_sched* s, cudaStream_t st) {
-  for (size_t g = 0; g < s->groups.size(); ++g) {
-    const int N = std::get<0>(s->groups[g]), prec = std::get<1>(s->groups[g]);
-    const bool shell = std::get<2>(s->groups[g]) == NUMA_MESH_SHELL;
-    const bool affine = std::get<3>(s->groups[g]) != 0;
-    for (int stage = 0; stage < 3; ++stage) {
-      const MemberDesc* d = s->d_desc + (size_t)stage * kMaxMembers;
-      cudaError_t e = launch_volume_ragged(N, prec, affine, d, s->d_groups + g, st);
-      if (e == cudaSuccess) e = launch_update_ragged(prec, shell, stage, d, s->d_groups + g, st);
-      if (e != cudaSuccess) return e;
-    }
+// state differs between the first and the later stages).  Groups share no
+// member, so with more than one group each takes a branch stream forked
+// from st and joined back into it (st being captured, the branches become
+// parallel paths of the step graph).
+cudaError_t enqueue_group(numa_sched* s, size_t g, cudaStream_t st) {
+  const int N = std::get<0>(s->groups[g]), prec = std::get<1>(s->groups[g]);
+  const bool shell = std::get<2>(s->groups[g]) == NUMA_MESH_SHELL;
+  const bool affine = std::get<3>(s->groups[g]) != 0;
+  for (int stage = 0; stage < 3; ++stage) {
+    const MemberDesc* d = s->d_desc + (size_t)stage * kMaxMembers;
+    cudaError_t e = launch_volume_ragged(N, prec, affine, d, s->d_groups + g, st);
+    if (e == cudaSuccess) e = launch_update_ragged(prec, shell, stage, d, s->d_groups + g, st);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t enqueue_step(numa_sched* s, cudaStream_t st) {
+  const size_t ng = s->groups.size();
+  const int nb = ng < (size_t)kBranches ? (int)ng : kBranches;
+  if (nb <= 1) return ng ? enqueue_group(s, 0, st) : cudaSuccess;
+  cudaError_t e = cudaEventRecord(s->fork, st);
+  for (int b = 1; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(s->branch[b], s->fork, 0);
+  for (size_t g = 0; g < ng && e == cudaSuccess; ++g) {
+    const int b = (int)(g % (size_t)nb);
+    e = enqueue_group(s, g, b ? s->branch[b] : st);
+  }
+  // join every branch that was forked, also after an error, so that the
+  // capture ends cleanly
+  for (int b = 1; b < nb; ++b) {
+    cudaError_t ej = cudaEventRecord(s->join[b], s->branch[b]);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, s->join[b], 0);
+    if (e == cudaSuccess) e = ej;
+  }
+  return e;
 }
 
 cudaError_t upload_tables(numa_sched* s) {
@@ -308,6 +338,11 @@ int numa_sched_create(void* dev_arena, size_t arena_bytes, void* stream, int bui
   s->alloc.init(arena_bytes - tables);
   cudaError_t e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+  for (int b = 1; b < kBranches && e == cudaSuccess; ++b) {
+    e = cudaStreamCreateWithFlags(&s->branch[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_desc, sizeof(MemberDesc) * 3 * kMaxMembers);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_groups, sizeof(RaggedGroup) * kMaxGroups);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->tables_copied, cudaEventDisableTiming);
@@ -564,6 +599,11 @@ int numa_sched_destroy(numa_sched* s) {
   if (s->h_groups) cudaFreeHost(s->h_groups);
   if (s->upload) cudaStreamDestroy(s->upload);
   if (s->cap) cudaStreamDestroy(s->cap);
+  for (int b = 1; b < kBranches; ++b) {
+    if (s->branch[b]) cudaStreamDestroy(s->branch[b]);
+    if (s->join[b]) cudaEventDestroy(s->join[b]);
+  }
+  if (s->fork) cudaEventDestroy(s->fork);
   delete s;
   return NUMA_OK;
 }
