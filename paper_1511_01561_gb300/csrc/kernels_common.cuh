@@ -138,6 +138,14 @@ __device__ __forceinline__ Pairs pp_norm(float sh, float sl) {
   return {s, sl - (s - sh)};
 }
 
+// a + b (TwoSum of the high parts, low parts added in).
+__device__ __forceinline__ Pairs pp_add(Pairs a, Pairs b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float t = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
+  return pp_norm(s, t);
+}
+
 // a - b (TwoSum of the high parts, low parts added in).
 __device__ __forceinline__ Pairs pp_sub(Pairs a, Pairs b) {
   const float s = a.h - b.h;
@@ -901,6 +909,98 @@ __device__ __forceinline__ void volume_element_pairs_affine(const VolumeArgs& a,
   }
 }
 
+// create_rhs of a rectilinear affine element in the pairs mode: the folded
+// form of volume_element_rect (weighted D, per-element K_d, no metric or Jw
+// per node) in (hi, lo) float pairs.  Along every contraction line the
+// weight beta_d = K_d w w is constant, so the line's common level cancels if
+// the unweighted fluxes are taken less their values at element node 0
+// before they are weighted: Dw annihilates constants as D does.  p' enters
+// less its value at node 0 as well (as in volume_element_pairs_affine).  The
+// 12 unweighted fields are those of volume_element_nodal64 (pressure on the
+// diagonal, the symmetric momentum flux stored once).  smem_raw holds
+// 15 (N+1)^3 + (N+1)^2 + 15 pairs.
+template <int N>
+__device__ __forceinline__ void volume_element_pairs_rect(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
+  constexpr int P = N + 1, NP = P * P * P;
+  Pairs* G = reinterpret_cast<Pairs*>(smem_raw);  // [15][NP]
+  Pairs* Ds = G + 15 * NP;                         // [P][P]: Dw
+  Pairs* base = Ds + P * P;                        // [kLF]: the unweighted fluxes at element node 0
+  const int l = threadIdx.x;
+  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = split64(a.Dw64[t]);
+  const long long e0 = e * NP, n = e0 + l;
+  const long long Ng = a.Ng, Nl = a.Nl;
+  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  Pairs f[kLF];
+  if (l < NP) {
+    const int g = a.l2g[n];
+    const Pairs* w = static_cast<const Pairs*>(a.prim);
+    const Pairs Ux = w[g], Uy = w[Ng + g], Uz = w[2 * Ng + g];
+    const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
+    const Pairs th = w[6 * Ng + g];
+    const Pairs pp = pp_sub(w[7 * Ng + g], w[7 * Ng + a.l2g[e0]]);
+    f[lUx] = Ux;
+    f[lUy] = Uy;
+    f[lUz] = Uz;
+    f[lTxx] = pp_add(pp_mul(Ux, ux), pp);
+    f[lTyy] = pp_add(pp_mul(Uy, uy), pp);
+    f[lTzz] = pp_add(pp_mul(Uz, uz), pp);
+    f[lTxy] = pp_mul(Ux, uy);
+    f[lTxz] = pp_mul(Ux, uz);
+    f[lTyz] = pp_mul(Uy, uz);
+    f[lHx] = pp_mul(th, Ux);
+    f[lHy] = pp_mul(th, Uy);
+    f[lHz] = pp_mul(th, Uz);
+    if (l == 0) {
+#pragma unroll
+      for (int t = 0; t < kLF; ++t) base[t] = f[t];
+    }
+  }
+  __syncthreads();
+  if (l < NP) {
+    const long long Ne = a.Ne;
+    const Pairs b0 = pp_mul(split64(a.affk[e]), split64(a.ww64[j * P + k]));
+    const Pairs b1 = pp_mul(split64(a.affk[Ne + e]), split64(a.ww64[i * P + k]));
+    const Pairs b2 = pp_mul(split64(a.affk[2 * Ne + e]), split64(a.ww64[i * P + j]));
+#pragma unroll
+    for (int t = 0; t < kLF; ++t) f[t] = pp_sub(f[t], base[t]);
+    // [3v + d]: equation v's flux along x_d, weighted by beta_d
+    G[0 * NP + l] = pp_mul(b0, f[lUx]);
+    G[1 * NP + l] = pp_mul(b1, f[lUy]);
+    G[2 * NP + l] = pp_mul(b2, f[lUz]);
+    G[3 * NP + l] = pp_mul(b0, f[lTxx]);
+    G[4 * NP + l] = pp_mul(b1, f[lTxy]);
+    G[5 * NP + l] = pp_mul(b2, f[lTxz]);
+    G[6 * NP + l] = pp_mul(b0, f[lTxy]);
+    G[7 * NP + l] = pp_mul(b1, f[lTyy]);
+    G[8 * NP + l] = pp_mul(b2, f[lTyz]);
+    G[9 * NP + l] = pp_mul(b0, f[lTxz]);
+    G[10 * NP + l] = pp_mul(b1, f[lTyz]);
+    G[11 * NP + l] = pp_mul(b2, f[lTzz]);
+    G[12 * NP + l] = pp_mul(b0, f[lHx]);
+    G[13 * NP + l] = pp_mul(b1, f[lHy]);
+    G[14 * NP + l] = pp_mul(b2, f[lHz]);
+  }
+  __syncthreads();
+  if (l >= NP) return;
+  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  double* re = static_cast<double*>(a.re);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const Pairs* g0 = G + (3 * v) * NP;
+    const Pairs* g1 = g0 + NP;
+    const Pairs* g2 = g1 + NP;
+    float h, lo;
+    pp_first(h, lo, Ds[i * P], g0[bx]);
+#pragma unroll
+    for (int m = 1; m < P; ++m) pp_fma(h, lo, Ds[i * P + m], g0[bx + m]);
+#pragma unroll
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[j * P + m], g1[by + P * m]);
+#pragma unroll
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[k * P + m], g2[bz + P * P * m]);
+    re[v * Nl + n] = join64(pp_norm(h, lo));
+  }
+}
+
 // Dynamic shared memory of one element: the staged fluxes, D and (pairs
 // mode) the node-0 base values.
 template <int N, typename T, bool AFF>
@@ -917,8 +1017,13 @@ constexpr size_t element_smem_bytes() {
 template <int N, typename T, bool AFF>
 __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   if constexpr (std::is_same<T, Pairs>::value) {
-    if constexpr (AFF) volume_element_pairs_affine<N>(a, e, smem_raw);
-    else volume_element_pairs<N>(a, e, smem_raw);
+    if constexpr (AFF) {
+      // uniform over the CTA: rectilinear elements take the folded form
+      if (a.affine == 2) volume_element_pairs_rect<N>(a, e, smem_raw);
+      else volume_element_pairs_affine<N>(a, e, smem_raw);
+    } else {
+      volume_element_pairs<N>(a, e, smem_raw);
+    }
   } else if constexpr (std::is_same<T, float>::value) {
     volume_element_lines<N, AFF>(a, e, smem_raw);
   } else if constexpr (AFF) {

@@ -464,7 +464,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
     d.nrm = (double*)take(3 * Ng * 8);
   }
   d.D64 = (double*)take(PP * 8);
-  if (c.precision == NUMA_FP64 && affine_elements(c)) {
+  if ((c.precision == NUMA_FP64 || c.precision == NUMA_FP64_PAIRS) && affine_elements(c)) {
     d.affk = (double*)take(3 * (size_t)m.Ne * 8);
     d.Dw64 = (double*)take(PP * 8);
     d.ww64 = (double*)take(PP * 8);
@@ -601,13 +601,13 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.D32, D32.data(), D32.size() * 4);
   up(L.D2, D2.data(), D2.size() * 4);
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
-  // FP64: the weighted metric of the per-node form, or the per-element
-  // constants of rectilinear elements
+  // FP64: the weighted metric of the per-node form; FP64 and pairs: the
+  // per-element constants of rectilinear elements
   std::vector<double> affk, Dw, ww;
   bool rect = false;
-  if (c->cfg.precision == NUMA_FP64) {
+  if (c->cfg.precision == NUMA_FP64 || c->cfg.precision == NUMA_FP64_PAIRS) {
     if (!affine_elements(c->cfg)) {
-      if (e == cudaSuccess && Nl)
+      if (c->cfg.precision == NUMA_FP64 && e == cudaSuccess && Nl)
         weight_metric_kernel<<<(unsigned)((Nl + 255) / 256), 256, 0, s>>>(L.met64, (long long)Nl);
       if (e == cudaSuccess) e = cudaGetLastError();
     } else {
