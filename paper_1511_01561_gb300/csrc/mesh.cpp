@@ -288,6 +288,19 @@ bool build_host_mesh(const numa_config& c, HostMesh& m, std::string& err) {
   lobatto(m.N, m.xi, m.w);
   diffmat(m.xi, m.D);
   std::vector<double> X;
+  // element nodes from the configuration alone, so that a mesh beyond the
+  // 32-bit indices is refused before any of its arrays is built (each global
+  // node belongs to at least one element node, so Nl bounds Ng as well)
+  {
+    const double np = (double)(c.N + 1) * (c.N + 1) * (c.N + 1);
+    double ne = 0.0;
+    if (c.mesh_kind == NUMA_MESH_BOX) ne = (double)c.nex * c.ney * c.nez;
+    else if (c.mesh_kind == NUMA_MESH_SHELL) ne = 6.0 * c.npanel * c.npanel * c.nlayer;
+    if (ne * np >= 2147483648.0) {
+      err = "mesh too large for 32-bit node indices";
+      return false;
+    }
+  }
   if (c.mesh_kind == NUMA_MESH_BOX) {
     if (c.nex < 1 || c.ney < 1 || c.nez < 1 || !(c.Lx > 0) || !(c.Ly > 0) || !(c.Lz > 0)) {
       err = "box needs positive element counts and extents";

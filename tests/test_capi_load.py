@@ -116,6 +116,25 @@ def test_argument_errors_without_gpu(numa):
     assert numa.lib.numa_rhs(None, None, None) == -1
 
 
+def test_meshes_beyond_32_bit_indices_are_refused(numa):
+    """Node indices are 32-bit: a mesh with 2^31 or more element nodes is
+    refused (NUMA_EINVAL) from its configuration, before any of its arrays is
+    built (so at once, without the tens of GB its host arrays would take).
+    At N=4 (125 element nodes per element) the largest cubic box below the
+    limit has 258^3 elements."""
+    import time
+    assert 258 ** 3 * 125 < 2 ** 31 <= 259 ** 3 * 125
+    for cfg in (I.box(259, 4), I.box((1024, 1024, 17), 4), I.shell(200, 100, 4)):
+        ne = (6 * cfg["npanel"] ** 2 * cfg["nlayer"] if cfg["kind"] == "shell"
+              else cfg["ne"][0] * cfg["ne"][1] * cfg["ne"][2])
+        assert ne * (cfg["N"] + 1) ** 3 >= 2 ** 31  # never build a mesh of that size here
+        t0 = time.perf_counter()
+        with pytest.raises(numa.NumaError) as e:
+            numa.numa_create(cfg)
+        assert e.value.code == -1
+        assert time.perf_counter() - t0 < 1.0
+
+
 @pytest.mark.parametrize("cfg,want,expect", [
     (dict(I.box(32, 4), precision="fp32_mixed"), 0, 4),  # FP32-mixed, 2.1M nodes: four by default
     (I.box(32, 4), 0, 1),                       # FP64: none by default
