@@ -711,45 +711,51 @@ __device__ __forceinline__ void volume_element_lines(const VolumeArgs& a, long l
   }
 }
 
-// create_rhs of element e in the pairs mode: the same steps as
-// volume_element, every value and product carried as a (hi, lo) float pair.
+// create_rhs of element e in the pairs mode: the steps of
+// volume_element_nodal64 (12 flux fields with the pressure on the diagonal,
+// metric terms pre-multiplied by -Jw: rows 0..8 of met2 hold -Jw dxi_d/dx_c
+// for this form), every value and product carried as a (hi, lo) float pair.
+// The fluxes are differentiated less their values at element node 0, and
+// p' enters less its node-0 value, so that the 48-bit products round at the
+// level of the fields' variation, not of their common level.  smem_raw
+// holds 12 (N+1)^3 + (N+1)^2 + 12 pairs.
 template <int N>
 __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   constexpr int P = N + 1, NP = P * P * P;
-  Pairs* F = reinterpret_cast<Pairs*>(smem_raw);  // [kNF][NP]
-  Pairs* Ds = F + kNF * NP;                         // [P][P]
-  Pairs* base = Ds + P * P;                         // [kNF]: the fluxes at element node 0
+  Pairs* F = reinterpret_cast<Pairs*>(smem_raw);  // [kLF][NP]
+  Pairs* Ds = F + kLF * NP;                         // [P][P]
+  Pairs* base = Ds + P * P;                         // [kLF]: the fluxes at element node 0
   const Pairs* Dg = reinterpret_cast<const Pairs*>(a.D2);
   const Pairs* met = reinterpret_cast<const Pairs*>(a.met2);
   const int l = threadIdx.x;
   for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
-  const long long n = e * NP + l;
+  const long long e0 = e * NP, n = e0 + l;
   const long long Ng = a.Ng, Nl = a.Nl;
   if (l < NP) {
     const int g = a.l2g[n];
     const Pairs* w = static_cast<const Pairs*>(a.prim);
     const Pairs Ux = w[g], Uy = w[Ng + g], Uz = w[2 * Ng + g];
     const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
-    const Pairs th = w[6 * Ng + g], pp = w[7 * Ng + g];
-    Pairs v[kNF];
-    v[kUx] = Ux;
-    v[kUy] = Uy;
-    v[kUz] = Uz;
-    v[kTxx] = pp_mul(Ux, ux);
-    v[kTxy] = pp_mul(Ux, uy);
-    v[kTxz] = pp_mul(Ux, uz);
-    v[kTyy] = pp_mul(Uy, uy);
-    v[kTyz] = pp_mul(Uy, uz);
-    v[kTzz] = pp_mul(Uz, uz);
-    v[kPp] = pp;
-    v[kHx] = pp_mul(th, Ux);
-    v[kHy] = pp_mul(th, Uy);
-    v[kHz] = pp_mul(th, Uz);
+    const Pairs th = w[6 * Ng + g];
+    const Pairs pp = pp_sub(w[7 * Ng + g], w[7 * Ng + a.l2g[e0]]);
+    Pairs v[kLF];
+    v[lUx] = Ux;
+    v[lUy] = Uy;
+    v[lUz] = Uz;
+    v[lTxx] = pp_add(pp_mul(Ux, ux), pp);
+    v[lTyy] = pp_add(pp_mul(Uy, uy), pp);
+    v[lTzz] = pp_add(pp_mul(Uz, uz), pp);
+    v[lTxy] = pp_mul(Ux, uy);
+    v[lTxz] = pp_mul(Ux, uz);
+    v[lTyz] = pp_mul(Uy, uz);
+    v[lHx] = pp_mul(th, Ux);
+    v[lHy] = pp_mul(th, Uy);
+    v[lHz] = pp_mul(th, Uz);
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) F[f * NP + l] = v[f];
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = v[f];
     if (l == 0) {
 #pragma unroll
-      for (int f = 0; f < kNF; ++f) base[f] = v[f];
+      for (int f = 0; f < kLF; ++f) base[f] = v[f];
     }
   }
   __syncthreads();
@@ -759,15 +765,14 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   // thread rewrites only its own node's entries.
   if (l < NP) {
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) F[f * NP + l] = pp_sub(F[f * NP + l], base[f]);
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = pp_sub(F[f * NP + l], base[f]);
   }
   __syncthreads();
   if (l >= NP) return;
   const int i = l % P, j = (l / P) % P, k = l / (P * P);
-  Pairs B[9];
+  Pairs B[9];  // -Jw dxi_d/dx_c at this node, [3d + c]
 #pragma unroll
   for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + n];
-  const Pairs jw = met[9 * Nl + n];
   const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
   // reference-space derivatives (Eq. 5) as normalised pairs
   auto dref = [&](int f, Pairs& s0, Pairs& s1, Pairs& s2) {
@@ -786,7 +791,7 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
     s1 = pp_norm(h1, l1);
     s2 = pp_norm(h2, l2);
   };
-  // chain rule: accumulate d/dx_c of a field into the unnormalised (dh, dl)
+  // chain rule into the weighted divergence: (dh, dl) += -Jw d/dx_c of a field
   auto phys = [&](float& dh, float& dl, bool first, int c, Pairs s0, Pairs s1, Pairs s2) {
     if (first) pp_first(dh, dl, s0, B[c]);
     else pp_fma(dh, dl, s0, B[c]);
@@ -795,29 +800,25 @@ __device__ __forceinline__ void volume_element_pairs(const VolumeArgs& a, long l
   };
   Pairs s0, s1, s2;
   float rh, rl, xh, xl, yh, yl, zh, zl, th_, tl;
-  dref(kUx, s0, s1, s2); phys(rh, rl, true, 0, s0, s1, s2);
-  dref(kUy, s0, s1, s2); phys(rh, rl, false, 1, s0, s1, s2);
-  dref(kUz, s0, s1, s2); phys(rh, rl, false, 2, s0, s1, s2);
-  dref(kTxx, s0, s1, s2); phys(xh, xl, true, 0, s0, s1, s2);
-  dref(kTxy, s0, s1, s2); phys(xh, xl, false, 1, s0, s1, s2); phys(yh, yl, true, 0, s0, s1, s2);
-  dref(kTxz, s0, s1, s2); phys(xh, xl, false, 2, s0, s1, s2); phys(zh, zl, true, 0, s0, s1, s2);
-  dref(kTyy, s0, s1, s2); phys(yh, yl, false, 1, s0, s1, s2);
-  dref(kTyz, s0, s1, s2); phys(yh, yl, false, 2, s0, s1, s2); phys(zh, zl, false, 1, s0, s1, s2);
-  dref(kTzz, s0, s1, s2); phys(zh, zl, false, 2, s0, s1, s2);
-  dref(kPp, s0, s1, s2);
-  phys(xh, xl, false, 0, s0, s1, s2);
-  phys(yh, yl, false, 1, s0, s1, s2);
-  phys(zh, zl, false, 2, s0, s1, s2);
-  dref(kHx, s0, s1, s2); phys(th_, tl, true, 0, s0, s1, s2);
-  dref(kHy, s0, s1, s2); phys(th_, tl, false, 1, s0, s1, s2);
-  dref(kHz, s0, s1, s2); phys(th_, tl, false, 2, s0, s1, s2);
-  // element residual -Jw div F in FP64 (the pair is exact in a double)
+  dref(lUx, s0, s1, s2); phys(rh, rl, true, 0, s0, s1, s2);
+  dref(lUy, s0, s1, s2); phys(rh, rl, false, 1, s0, s1, s2);
+  dref(lUz, s0, s1, s2); phys(rh, rl, false, 2, s0, s1, s2);
+  dref(lTxx, s0, s1, s2); phys(xh, xl, true, 0, s0, s1, s2);
+  dref(lTyy, s0, s1, s2); phys(yh, yl, true, 1, s0, s1, s2);
+  dref(lTzz, s0, s1, s2); phys(zh, zl, true, 2, s0, s1, s2);
+  dref(lTxy, s0, s1, s2); phys(xh, xl, false, 1, s0, s1, s2); phys(yh, yl, false, 0, s0, s1, s2);
+  dref(lTxz, s0, s1, s2); phys(xh, xl, false, 2, s0, s1, s2); phys(zh, zl, false, 0, s0, s1, s2);
+  dref(lTyz, s0, s1, s2); phys(yh, yl, false, 2, s0, s1, s2); phys(zh, zl, false, 1, s0, s1, s2);
+  dref(lHx, s0, s1, s2); phys(th_, tl, true, 0, s0, s1, s2);
+  dref(lHy, s0, s1, s2); phys(th_, tl, false, 1, s0, s1, s2);
+  dref(lHz, s0, s1, s2); phys(th_, tl, false, 2, s0, s1, s2);
+  // the weighted residual -Jw div F of Eq. 4 in FP64 (the pair is exact in a double)
   double* re = static_cast<double*>(a.re);
-  re[n] = -join64(pp_mul(jw, pp_norm(rh, rl)));
-  re[Nl + n] = -join64(pp_mul(jw, pp_norm(xh, xl)));
-  re[2 * Nl + n] = -join64(pp_mul(jw, pp_norm(yh, yl)));
-  re[3 * Nl + n] = -join64(pp_mul(jw, pp_norm(zh, zl)));
-  re[4 * Nl + n] = -join64(pp_mul(jw, pp_norm(th_, tl)));
+  re[n] = join64(pp_norm(rh, rl));
+  re[Nl + n] = join64(pp_norm(xh, xl));
+  re[2 * Nl + n] = join64(pp_norm(yh, yl));
+  re[3 * Nl + n] = join64(pp_norm(zh, zl));
+  re[4 * Nl + n] = join64(pp_norm(th_, tl));
 }
 
 // create_rhs of an affine element in the pairs mode: the contravariant
@@ -1010,7 +1011,7 @@ constexpr size_t element_smem_bytes() {
   if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (15 * NP + P * P);
   if constexpr (std::is_same<T, double>::value) return sizeof(T) * (kLF * NP + P * P);
   if constexpr (AFF) return sizeof(T) * (15 * NP + P * P + 15);
-  return sizeof(T) * (kNF * NP + P * P + kNF);
+  return sizeof(T) * (kLF * NP + P * P + kLF);
 }
 
 // Element kernel of one precision; AFF selects the affine-element form.

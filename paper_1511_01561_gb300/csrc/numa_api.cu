@@ -589,7 +589,18 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
     for (size_t t = 0; t < m.met.size(); ++t) met32[t] = (float)m.met[t];
     up(L.met32, met32.data(), met32.size() * 4);
   } else if (c->cfg.precision == NUMA_FP64_PAIRS) {
-    met32 = pairs_of(m.met);
+    if (affine_elements(c->cfg)) {
+      met32 = pairs_of(m.met);
+    } else {
+      // the per-node pairs form reads rows 0..8 as -Jw dxi_d/dx_c (row 9,
+      // Jw itself, stays for the filter): weighted in FP64, then split
+      std::vector<double> wm(m.met);
+      for (size_t n = 0; n < Nl; ++n) {
+        const double jw = m.met[9 * Nl + n];
+        for (int t = 0; t < 9; ++t) wm[t * Nl + n] = -jw * m.met[t * Nl + n];
+      }
+      met32 = pairs_of(wm);
+    }
     up(L.met2, met32.data(), met32.size() * 4);
   } else {
     up(L.met64, m.met.data(), m.met.size() * 8);

@@ -185,7 +185,10 @@ def test_imex_parity_shell(numa, orc, name, cfg, dt, nsteps, nu, precision):
         sv.close()
     ref = ref[:, perm]
     err = rel_errors(got, ref, state_floors(ref, m.ref()[0].max()))
-    assert err.max() <= 1e-10, err
+    # the pairs mode's stated bar on curved elements: 2^(53-48) = 32 times
+    # the FP64 bar (48-bit pair arithmetic; tests/test_gpu_parity.py)
+    tol = 1e-10 * (32.0 if precision == "fp64_pairs" else 1.0)
+    assert err.max() <= tol, err
 
 
 @pytest.mark.gpu
