@@ -110,19 +110,39 @@ def ncu_traffic(key: str, workload: str):
     return NCU_TRAFFIC.get(key)
 
 
+def volume_fp64_cost(N: int, form: str) -> tuple:
+    """(flops, FP64 operations) per element node of the FP64 element kernel
+    of `form`.  A flop count takes an FMA as 2; an operation count takes an
+    FMA, a product and a sum as 1 each (each takes one slot of the FP64 pipe).
+    - "nodal", the per-node form of Eq. 5 (any element): 12 flux fields
+      (U, the symmetric U (x) u + p' I, theta U: 9 operations, 12 flops),
+      each differentiated along xi, eta and zeta (3 (N+1) operations,
+      6 (N+1) - 3 flops), and 15 uses of a derivative triple folded into
+      their equations with the -Jw-weighted metric (3 operations, 6 flops):
+      9 + 36 (N+1) + 45 operations, 72 (N+1) + 107 flops.
+    - "rect", rectilinear affine elements: the same 12 fields; per equation
+      three contractions of length N+1 with K_d D (3 (N+1) operations, the
+      first a product: 6 (N+1) - 1 flops) and one product by w_i w_j w_k;
+      the element's K_d D, 3 (N+1)^2 products shared by its (N+1)^3 nodes:
+      14 + 15 (N+1) + 3 / (N+1) operations, 12 + 5 (6 (N+1) - 1) + 5 +
+      3 / (N+1) flops.
+    - "affine", affine elements with a full metric: per direction B_d.u and
+      B_d.U (3 operations, 5 flops each), three momentum fluxes
+      U_c (B_d.u) + B_dc p' (2 operations, 3 flops each) and theta (B_d.U)
+      (1), then 15 contractions of length N+1 and 5 products with -Jw:
+      44 + 15 (N+1) operations, 30 (N+1) + 65 flops."""
+    P = N + 1
+    if form == "rect":
+        return 12.0 + 5.0 * (6 * P - 1) + 5.0 + 3.0 / P, 14.0 + 15.0 * P + 3.0 / P
+    if form == "affine":
+        return 30.0 * P + 65.0, 44.0 + 15.0 * P
+    return 72.0 * P + 107.0, 9.0 + 36.0 * P + 45.0
+
+
 def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
-    """Algorithmic flops per element node of create_rhs (an FMA counts 2).
-    Per-node form of Eq. 5: the flux tensor has 12 distinct components (U,
-    the symmetric U (x) u + p' I, theta U), each differentiated along the
-    three reference directions (36 contractions of length N+1, 72 (N+1)
-    flops); the chain rule folds each of the 15 uses of a derivative triple
-    into its equation (15 x 3 multiply-adds, 90 flops); building the fluxes
-    takes 12 flops and the -Jw weights 5: 72 (N+1) + 107.  Affine-element
-    form: 15 contractions of length N+1 plus 65 pointwise flops (per
-    direction: B_d.u and B_d.U, 5 each; three momentum fluxes
-    U_x (B_d.u) + B_dx p', 3 each; theta (B_d.U), 1; then 5 products with
-    -Jw)."""
-    return 30.0 * (N + 1) + 65.0 if affine else 72.0 * (N + 1) + 107.0
+    """Flops per element node of the FP64 element kernel that a box
+    (rectilinear elements, affine=True) or a curved mesh takes."""
+    return volume_fp64_cost(N, "rect" if affine else "nodal")[0]
 
 
 def filter_flops_per_elem_node(N: int) -> float:
@@ -409,8 +429,11 @@ def run_mine(args):
     value = whole_job_rate(world, Ng, args.steps, ms)
     nlaunch = STAGES * args.steps
     vol_avg_s = ms_vol * 1e-3 / nlaunch
-    flops = volume_flops_per_elem_node(N, affine) * Nl
+    fl_el, ops_el = volume_fp64_cost(N, "rect" if affine else "nodal")
+    flops = fl_el * Nl
     achieved_tf = flops / vol_avg_s / 1e12
+    # FP64 pipe slots: 2 per SM per clock, i.e. half the FMA flop peak
+    pipe_frac = ops_el * Nl / vol_avg_s / (FP64_PEAK_TFLOPS * 1e12 / 2)
     form_name = "affine" if affine else "nodal"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,10 +445,13 @@ def run_mine(args):
                    "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
         "e2e": e2e,
         "gpu_launches": 2 * nlaunch,
-        "roofline": {"kernel": f"volume_kernel<{N},double,{form_name}>", "bound": "alu", "achieved": achieved_tf,
+        "roofline": {"kernel": f"volume_kernel<{N},double,{form_name}>",
+                     "form": "rectilinear (K_d D, w_i w_j w_k)" if affine else "per-node (Eq. 5)",
+                     "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                      "traffic": ncu_traffic(f"volume_fp64_{form_name}", args.workload),
-                     "algorithmic_flops": flops,
+                     "algorithmic_flops": flops, "fp64_ops_per_element_node": ops_el,
+                     "fp64_pipe_frac": pipe_frac,
                      "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine),
                      "peak_source": FP64_PEAK_SOURCE,
                      "avg_launch_ms": 1e3 * vol_avg_s,
@@ -456,12 +482,14 @@ def run_mine(args):
         msn, voln, updn, _, _, _, finn, _ = measure("fp64", "nodal")
         voln_s = voln * 1e-3 / nlaunch
         fl_n = volume_flops_per_elem_node(N, False) * Nl
+        op_n = volume_fp64_cost(N, "nodal")[1] * Nl
         line["fp64_nodal_form"] = {
             "value": world * Ng * STAGES * args.steps / (msn * 1e-3), "unit": UNIT, "ms_per_step": msn / args.steps,
             "finite": finn, "volume_ms_avg": 1e3 * voln_s, "update_ms_avg": updn / nlaunch,
             "roofline": {"kernel": f"volume_kernel<{N},double,nodal>", "bound": "alu",
                          "achieved": fl_n / voln_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": fl_n / voln_s / 1e12 / FP64_PEAK_TFLOPS,
+                         "fp64_pipe_frac": op_n / voln_s / (FP64_PEAK_TFLOPS * 1e12 / 2),
                          "traffic": ncu_traffic("volume_fp64_nodal", args.workload)},
         }
     if not args.no_fp32:
@@ -538,11 +566,13 @@ def run_mine(args):
             sh[prec] = {"value": whole_job_rate(world, infos["Ng"], args.steps, mss), "ms_per_step": mss / args.steps,
                         "volume_ms_avg": vols / nl, "update_ms_avg": upds / nl, "finite": fins}
             if prec == "fp64":
-                fl_s = volume_flops_per_elem_node(infos["N"], False) * infos["Nl"]
+                fl_e, op_e = volume_fp64_cost(infos["N"], "nodal")
+                t_s = vols * 1e-3 / nl
                 sh[prec]["roofline"] = {"kernel": f"volume_kernel<{infos['N']},double,nodal>", "bound": "alu",
-                                        "achieved": fl_s / (vols * 1e-3 / nl) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                        "achieved": fl_e * infos["Nl"] / t_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                                         "unit": "TFLOP/s",
-                                        "frac": fl_s / (vols * 1e-3 / nl) / 1e12 / FP64_PEAK_TFLOPS}
+                                        "frac": fl_e * infos["Nl"] / t_s / 1e12 / FP64_PEAK_TFLOPS,
+                                        "fp64_pipe_frac": op_e * infos["Nl"] / t_s / (FP64_PEAK_TFLOPS * 1e12 / 2)}
             if prec == "fp32_mixed":
                 b32 = volume_bytes(infos["Nl"], infos["Ng"], 4)
                 sh[prec]["speedup_vs_fp64"] = sh[prec]["value"] / sh["fp64"]["value"]

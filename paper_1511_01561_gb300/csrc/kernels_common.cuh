@@ -392,12 +392,12 @@ __host__ __device__ constexpr int line_group() {
 //     13) and the metric terms are stored pre-multiplied by -Jw, so the chain
 //     rule is three FMAs per use of a field and no final weighting remains.
 // (2) Rectilinear affine elements (every element of an unwarped box): the
-//     metric terms dxi_d/dx_c vanish for c != d and, with J constant over the
-//     element, -Jw dxi_d/dx_d at node (i,j,k) is K_d w_j w_k for d = 0 (and
-//     likewise for d = 1, 2) with K_d = -J dxi_d/dx_d per element.  Folding
-//     w_i into D (Dw_im = w_i D_im) and the rest into the staged fluxes gives
-//     the weighted residual -Jw div F of Eq. 4 directly from 15 contractions,
-//     with no metric or Jw load per node.
+//     metric terms dxi_d/dx_c vanish for c != d and J is constant over the
+//     element, so -Jw div F at node (i,j,k) is w_i w_j w_k sum_d K_d (D F_d)
+//     along xi_d, with K_d = -J dxi_d/dx_d per element.  Folding K_d into the
+//     direction's copy of D (formed per element in shared memory) leaves the
+//     12 unweighted flux fields of (1), 15 contractions and one product by
+//     w_i w_j w_k per equation, with no metric or Jw load per node.
 
 // Flux fields of the FP64 per-node kernel: F_U = U (x) u + p' I with the
 // pressure in the diagonal components (the symmetric part stored once).
@@ -490,64 +490,67 @@ __device__ __forceinline__ void volume_element_nodal64(const VolumeArgs& a, long
 }
 
 // create_rhs of a rectilinear affine element in FP64 (see (2) above), one
-// thread per element node.  Node (i,j,k) stages, for each direction d, the
-// fluxes of the five equations along x_d scaled by beta_d = K_d w w (the two
-// Lobatto weights of the other directions):
-//   mass  beta_d U_d,  momentum beta_d U_c u_d (+ beta_d p' for c = d),
-//   Theta theta beta_d U_d,
-// and the weighted residual of equation v at (i,j,k) is then
-//   sum_m Dw_im G_v0(m,j,k) + sum_m Dw_jm G_v1(i,m,k) + sum_m Dw_km G_v2(i,j,m).
-// a.affk holds K_d per element [3][Ne], a.Dw64 Dw [P][P], a.ww64 w_i w_j
-// [P][P].  Shared memory: 15 (N+1)^3 + (N+1)^2 doubles.
+// thread per element node: 9 + 75 + 5 FP64 operations per node at N = 4.
+// a.affk holds K_d per element [3][Ne], a.w3_64 the weights w_i w_j w_k
+// [(N+1)^3].  Shared memory: 12 (N+1)^3 + 3 (N+1)^2 doubles.
 template <int N>
 __device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
-  constexpr int P = N + 1, NP = P * P * P;
-  double* G = reinterpret_cast<double*>(smem_raw);  // [15][NP]
-  double* Ds = G + 15 * NP;                         // [P][P]
+  constexpr int P = N + 1, PP = P * P, NP = PP * P;
+  double* F = reinterpret_cast<double*>(smem_raw);  // [kLF][NP]
+  double* Dk = F + kLF * NP;                         // [3][P][P]: K_d D
   const int l = threadIdx.x;
-  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = a.Dw64[t];
-  const long long Nl = a.Nl, e0 = (long long)e * NP, n = e0 + l;
-  const int i = l % P, j = (l / P) % P, k = l / (P * P);
+  for (int t = l; t < 3 * PP; t += blockDim.x) {
+    const int d = t / PP;
+    Dk[t] = a.affk[d * (long long)a.Ne + e] * a.D64[t - d * PP];
+  }
+  const long long Nl = a.Nl, n = (long long)e * NP + l;
   if (l < NP) {
-    const double K0 = a.affk[e], K1 = a.affk[a.Ne + e], K2 = a.affk[2 * (long long)a.Ne + e];
     const NodeState<double> z = gather_node<double>(a, n);
-    const double bt[3] = {K0 * a.ww64[j * P + k], K1 * a.ww64[i * P + k], K2 * a.ww64[i * P + j]};
-    const double U[3] = {z.Ux, z.Uy, z.Uz}, u[3] = {z.ux, z.uy, z.uz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const double Gr = bt[d] * U[d], ud = bt[d] * u[d], pd = bt[d] * z.pp;
-      G[d * NP + l] = Gr;
-      G[(3 + d) * NP + l] = d == 0 ? fma(z.Ux, ud, pd) : z.Ux * ud;
-      G[(6 + d) * NP + l] = d == 1 ? fma(z.Uy, ud, pd) : z.Uy * ud;
-      G[(9 + d) * NP + l] = d == 2 ? fma(z.Uz, ud, pd) : z.Uz * ud;
-      G[(12 + d) * NP + l] = z.th * Gr;
-    }
+    F[lUx * NP + l] = z.Ux;
+    F[lUy * NP + l] = z.Uy;
+    F[lUz * NP + l] = z.Uz;
+    F[lTxx * NP + l] = fma(z.Ux, z.ux, z.pp);
+    F[lTyy * NP + l] = fma(z.Uy, z.uy, z.pp);
+    F[lTzz * NP + l] = fma(z.Uz, z.uz, z.pp);
+    F[lTxy * NP + l] = z.Ux * z.uy;
+    F[lTxz * NP + l] = z.Ux * z.uz;
+    F[lTyz * NP + l] = z.Uy * z.uz;
+    F[lHx * NP + l] = z.th * z.Ux;
+    F[lHy * NP + l] = z.th * z.Uy;
+    F[lHz * NP + l] = z.th * z.Uz;
   }
   __syncthreads();
   if (l >= NP) return;
+  const int i = l % P, j = (l / P) % P, k = l / PP;
   double dx[P], dy[P], dz[P];
 #pragma unroll
   for (int m = 0; m < P; ++m) {
-    dx[m] = Ds[i * P + m];
-    dy[m] = Ds[j * P + m];
-    dz[m] = Ds[k * P + m];
+    dx[m] = Dk[i * P + m];
+    dy[m] = Dk[PP + j * P + m];
+    dz[m] = Dk[2 * PP + k * P + m];
   }
-  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  const int bx = P * (j + P * k), by = i + PP * k, bz = i + P * j;
+  const double w3 = a.w3_64[l];
+  // w_i w_j w_k (K_x D F_x along xi + K_y D F_y along eta + K_z D F_z along zeta)
+  auto div = [&](int fx, int fy, int fz) {
+    const double* gx = F + fx * NP;
+    const double* gy = F + fy * NP;
+    const double* gz = F + fz * NP;
+    double t = dx[0] * gx[bx];
+#pragma unroll
+    for (int m = 1; m < P; ++m) t = fma(dx[m], gx[bx + m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dy[m], gy[by + P * m], t);
+#pragma unroll
+    for (int m = 0; m < P; ++m) t = fma(dz[m], gz[bz + PP * m], t);
+    return w3 * t;
+  };
   double* re = static_cast<double*>(a.re);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const double* g0 = G + (3 * v) * NP;
-    const double* g1 = g0 + NP;
-    const double* g2 = g1 + NP;
-    double t = dx[0] * g0[bx];
-#pragma unroll
-    for (int m = 1; m < P; ++m) t = fma(dx[m], g0[bx + m], t);
-#pragma unroll
-    for (int m = 0; m < P; ++m) t = fma(dy[m], g1[by + P * m], t);
-#pragma unroll
-    for (int m = 0; m < P; ++m) t = fma(dz[m], g2[bz + P * P * m], t);
-    re[v * Nl + n] = t;
-  }
+  re[n] = div(lUx, lUy, lUz);
+  re[Nl + n] = div(lTxx, lTxy, lTxz);
+  re[2 * Nl + n] = div(lTxy, lTyy, lTyz);
+  re[3 * Nl + n] = div(lTxz, lTyz, lTzz);
+  re[4 * Nl + n] = div(lHx, lHy, lHz);
 }
 
 // create_rhs of element e in the FP32 form, organised by 1D lines of nodes
@@ -911,27 +914,25 @@ __device__ __forceinline__ void volume_element_pairs_affine(const VolumeArgs& a,
 }
 
 // create_rhs of a rectilinear affine element in the pairs mode: the folded
-// form of volume_element_rect (weighted D, per-element K_d, no metric or Jw
-// per node) in (hi, lo) float pairs.  Along every contraction line the
-// weight beta_d = K_d w w is constant, so the line's common level cancels if
-// the unweighted fluxes are taken less their values at element node 0
-// before they are weighted: Dw annihilates constants as D does.  p' enters
-// less its value at node 0 as well (as in volume_element_pairs_affine).  The
-// 12 unweighted fields are those of volume_element_nodal64 (pressure on the
-// diagonal, the symmetric momentum flux stored once).  smem_raw holds
-// 15 (N+1)^3 + (N+1)^2 + 15 pairs.
+// form of volume_element_rect (K_d D per direction, one product by
+// w_i w_j w_k per equation, no metric or Jw per node) in (hi, lo) float
+// pairs.  The 12 unweighted fields are differentiated less their values at
+// element node 0 (K_d D annihilates constants as D does), and p' enters less
+// its node-0 value (as in volume_element_pairs_affine).  smem_raw holds
+// 12 (N+1)^3 + 3 (N+1)^2 + 12 pairs.
 template <int N>
 __device__ __forceinline__ void volume_element_pairs_rect(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
-  constexpr int P = N + 1, NP = P * P * P;
-  Pairs* G = reinterpret_cast<Pairs*>(smem_raw);  // [15][NP]
-  Pairs* Ds = G + 15 * NP;                         // [P][P]: Dw
-  Pairs* base = Ds + P * P;                        // [kLF]: the unweighted fluxes at element node 0
+  constexpr int P = N + 1, PP = P * P, NP = PP * P;
+  Pairs* F = reinterpret_cast<Pairs*>(smem_raw);  // [kLF][NP]
+  Pairs* Dk = F + kLF * NP;                        // [3][P][P]: K_d D
+  Pairs* base = Dk + 3 * PP;                       // [kLF]: the fluxes at element node 0
   const int l = threadIdx.x;
-  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = split64(a.Dw64[t]);
+  for (int t = l; t < 3 * PP; t += blockDim.x) {
+    const int d = t / PP;
+    Dk[t] = split64(a.affk[d * (long long)a.Ne + e] * a.D64[t - d * PP]);
+  }
   const long long e0 = e * NP, n = e0 + l;
   const long long Ng = a.Ng, Nl = a.Nl;
-  const int i = l % P, j = (l / P) % P, k = l / (P * P);
-  Pairs f[kLF];
   if (l < NP) {
     const int g = a.l2g[n];
     const Pairs* w = static_cast<const Pairs*>(a.prim);
@@ -939,67 +940,56 @@ __device__ __forceinline__ void volume_element_pairs_rect(const VolumeArgs& a, l
     const Pairs ux = w[3 * Ng + g], uy = w[4 * Ng + g], uz = w[5 * Ng + g];
     const Pairs th = w[6 * Ng + g];
     const Pairs pp = pp_sub(w[7 * Ng + g], w[7 * Ng + a.l2g[e0]]);
-    f[lUx] = Ux;
-    f[lUy] = Uy;
-    f[lUz] = Uz;
-    f[lTxx] = pp_add(pp_mul(Ux, ux), pp);
-    f[lTyy] = pp_add(pp_mul(Uy, uy), pp);
-    f[lTzz] = pp_add(pp_mul(Uz, uz), pp);
-    f[lTxy] = pp_mul(Ux, uy);
-    f[lTxz] = pp_mul(Ux, uz);
-    f[lTyz] = pp_mul(Uy, uz);
-    f[lHx] = pp_mul(th, Ux);
-    f[lHy] = pp_mul(th, Uy);
-    f[lHz] = pp_mul(th, Uz);
+    Pairs v[kLF];
+    v[lUx] = Ux;
+    v[lUy] = Uy;
+    v[lUz] = Uz;
+    v[lTxx] = pp_add(pp_mul(Ux, ux), pp);
+    v[lTyy] = pp_add(pp_mul(Uy, uy), pp);
+    v[lTzz] = pp_add(pp_mul(Uz, uz), pp);
+    v[lTxy] = pp_mul(Ux, uy);
+    v[lTxz] = pp_mul(Ux, uz);
+    v[lTyz] = pp_mul(Uy, uz);
+    v[lHx] = pp_mul(th, Ux);
+    v[lHy] = pp_mul(th, Uy);
+    v[lHz] = pp_mul(th, Uz);
+#pragma unroll
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = v[f];
     if (l == 0) {
 #pragma unroll
-      for (int t = 0; t < kLF; ++t) base[t] = f[t];
+      for (int f = 0; f < kLF; ++f) base[f] = v[f];
     }
   }
   __syncthreads();
   if (l < NP) {
-    const long long Ne = a.Ne;
-    const Pairs b0 = pp_mul(split64(a.affk[e]), split64(a.ww64[j * P + k]));
-    const Pairs b1 = pp_mul(split64(a.affk[Ne + e]), split64(a.ww64[i * P + k]));
-    const Pairs b2 = pp_mul(split64(a.affk[2 * Ne + e]), split64(a.ww64[i * P + j]));
 #pragma unroll
-    for (int t = 0; t < kLF; ++t) f[t] = pp_sub(f[t], base[t]);
-    // [3v + d]: equation v's flux along x_d, weighted by beta_d
-    G[0 * NP + l] = pp_mul(b0, f[lUx]);
-    G[1 * NP + l] = pp_mul(b1, f[lUy]);
-    G[2 * NP + l] = pp_mul(b2, f[lUz]);
-    G[3 * NP + l] = pp_mul(b0, f[lTxx]);
-    G[4 * NP + l] = pp_mul(b1, f[lTxy]);
-    G[5 * NP + l] = pp_mul(b2, f[lTxz]);
-    G[6 * NP + l] = pp_mul(b0, f[lTxy]);
-    G[7 * NP + l] = pp_mul(b1, f[lTyy]);
-    G[8 * NP + l] = pp_mul(b2, f[lTyz]);
-    G[9 * NP + l] = pp_mul(b0, f[lTxz]);
-    G[10 * NP + l] = pp_mul(b1, f[lTyz]);
-    G[11 * NP + l] = pp_mul(b2, f[lTzz]);
-    G[12 * NP + l] = pp_mul(b0, f[lHx]);
-    G[13 * NP + l] = pp_mul(b1, f[lHy]);
-    G[14 * NP + l] = pp_mul(b2, f[lHz]);
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = pp_sub(F[f * NP + l], base[f]);
   }
   __syncthreads();
   if (l >= NP) return;
-  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
+  const int i = l % P, j = (l / P) % P, k = l / PP;
+  const int bx = P * (j + P * k), by = i + PP * k, bz = i + P * j;
+  const Pairs w3 = split64(a.w3_64[l]);
   double* re = static_cast<double*>(a.re);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const Pairs* g0 = G + (3 * v) * NP;
-    const Pairs* g1 = g0 + NP;
-    const Pairs* g2 = g1 + NP;
+  auto div = [&](int fx, int fy, int fz) {
+    const Pairs* gx = F + fx * NP;
+    const Pairs* gy = F + fy * NP;
+    const Pairs* gz = F + fz * NP;
     float h, lo;
-    pp_first(h, lo, Ds[i * P], g0[bx]);
+    pp_first(h, lo, Dk[i * P], gx[bx]);
 #pragma unroll
-    for (int m = 1; m < P; ++m) pp_fma(h, lo, Ds[i * P + m], g0[bx + m]);
+    for (int m = 1; m < P; ++m) pp_fma(h, lo, Dk[i * P + m], gx[bx + m]);
 #pragma unroll
-    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[j * P + m], g1[by + P * m]);
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Dk[PP + j * P + m], gy[by + P * m]);
 #pragma unroll
-    for (int m = 0; m < P; ++m) pp_fma(h, lo, Ds[k * P + m], g2[bz + P * P * m]);
-    re[v * Nl + n] = join64(pp_norm(h, lo));
-  }
+    for (int m = 0; m < P; ++m) pp_fma(h, lo, Dk[2 * PP + k * P + m], gz[bz + PP * m]);
+    return join64(pp_mul(w3, pp_norm(h, lo)));
+  };
+  re[n] = div(lUx, lUy, lUz);
+  re[Nl + n] = div(lTxx, lTxy, lTxz);
+  re[2 * Nl + n] = div(lTxy, lTyy, lTyz);
+  re[3 * Nl + n] = div(lTxz, lTyz, lTzz);
+  re[4 * Nl + n] = div(lHx, lHy, lHz);
 }
 
 // Dynamic shared memory of one element: the staged fluxes, D and (pairs

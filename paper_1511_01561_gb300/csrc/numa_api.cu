@@ -65,8 +65,7 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.D2 = c->L.D2;
   a.re = re;
   a.affk = c->L.affk;
-  a.Dw64 = c->L.Dw64;
-  a.ww64 = c->L.ww64;
+  a.w3_64 = c->L.w3_64;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
@@ -466,8 +465,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.D64 = (double*)take(PP * 8);
   if ((c.precision == NUMA_FP64 || c.precision == NUMA_FP64_PAIRS) && affine_elements(c)) {
     d.affk = (double*)take(3 * (size_t)m.Ne * 8);
-    d.Dw64 = (double*)take(PP * 8);
-    d.ww64 = (double*)take(PP * 8);
+    d.w3_64 = (double*)take(PP * m.P * 8);
   }
   d.D32 = (float*)take(PP * 4);
   d.D2 = (float2*)take(PP * 8);
@@ -614,7 +612,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
   // FP64: the weighted metric of the per-node form; FP64 and pairs: the
   // per-element constants of rectilinear elements
-  std::vector<double> affk, Dw, ww;
+  std::vector<double> affk, w3;
   bool rect = false;
   if (c->cfg.precision == NUMA_FP64 || c->cfg.precision == NUMA_FP64_PAIRS) {
     if (!affine_elements(c->cfg)) {
@@ -631,16 +629,12 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
         const double J = m.met[9 * Nl + n] / (w0 * w0 * w0);
         for (int d = 0; d < 3; ++d) affk[d * (size_t)m.Ne + el] = -J * m.met[(4 * d) * Nl + n];
       }
-      Dw.resize((size_t)P * P);
-      ww.resize((size_t)P * P);
-      for (int i = 0; i < P; ++i)
-        for (int j = 0; j < P; ++j) {
-          Dw[i * P + j] = m.w[i] * m.D[i * P + j];
-          ww[i * P + j] = m.w[i] * m.w[j];
-        }
+      w3.resize((size_t)P * P * P);
+      for (int k = 0; k < P; ++k)
+        for (int j = 0; j < P; ++j)
+          for (int i = 0; i < P; ++i) w3[i + P * (j + P * k)] = m.w[i] * m.w[j] * m.w[k];
       up(L.affk, affk.data(), affk.size() * 8);
-      up(L.Dw64, Dw.data(), Dw.size() * 8);
-      up(L.ww64, ww.data(), ww.size() * 8);
+      up(L.w3_64, w3.data(), w3.size() * 8);
     }
   }
   up(L.l2g, m.l2g.data(), Nl * 4);

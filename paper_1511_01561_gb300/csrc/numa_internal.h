@@ -76,9 +76,8 @@ struct DevLayout {
   double* gvec = nullptr;    // [3][Ng] (shell)
   double* nrm = nullptr;     // [3][Ng] (shell)
   double* D64 = nullptr;     // [P*P]
-  double* affk = nullptr;    // FP64 affine elements: [3][Ne] K_d = -J dxi_d/dx_d per element
-  double* Dw64 = nullptr;    // FP64 affine elements: [P*P] w_i D_ij
-  double* ww64 = nullptr;    // FP64 affine elements: [P*P] w_i w_j
+  double* affk = nullptr;    // FP64 / pairs affine elements: [3][Ne] K_d = -J dxi_d/dx_d per element
+  double* w3_64 = nullptr;   // FP64 / pairs affine elements: [P^3] w_i w_j w_k at local node i + P (j + P k)
   float* D32 = nullptr;      // [P*P]
   double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
@@ -120,9 +119,8 @@ struct VolumeArgs {
   const float2* met2;  // pairs mode
   const float2* D2;    // pairs mode
   void* re;            // [5][Nl] output
-  const double* affk;  // FP64 rectilinear form: [3][Ne] -J dxi_d/dx_d
-  const double* Dw64;  // FP64 rectilinear form: w_i D_ij
-  const double* ww64;  // FP64 rectilinear form: w_i w_j
+  const double* affk;   // rectilinear form (FP64, pairs): [3][Ne] -J dxi_d/dx_d
+  const double* w3_64;  // rectilinear form: [P^3] w_i w_j w_k
   long long Ng, Nl;
   int Ne;
   int ebeg, ecnt;      // the launch covers elements [ebeg, ebeg + ecnt) (a slab, or all: 0, Ne)

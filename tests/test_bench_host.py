@@ -14,12 +14,20 @@ import bench  # noqa: E402
 
 
 def test_flop_models():
-    # per-node form: 36 contractions of N+1 FMAs (12 flux components, 3
-    # directions), 45 chain-rule FMAs, 12 flux and 5 weight flops
-    assert bench.volume_flops_per_elem_node(4) == 72 * 5 + 107
-    # affine form: 15 contractions plus 65 pointwise flops
-    assert bench.volume_flops_per_elem_node(4, affine=True) == 30 * 5 + 65
-    assert bench.volume_flops_per_elem_node(1, affine=True) < bench.volume_flops_per_elem_node(1)
+    # per-node form at N=4: 9 flux operations, 12 fields x 3 directions x 5
+    # terms, 15 chain-rule triples (the kernel's "9 + 180 + 45")
+    fl, ops = bench.volume_fp64_cost(4, "nodal")
+    assert ops == 9 + 12 * 3 * 5 + 15 * 3 and fl == 72 * 5 + 107
+    # rectilinear form at N=4: 9 flux operations (3 FMAs, 6 products), 5
+    # equations x 15 terms (the first a product) and one weight product,
+    # K_d D: 75 products per 125 nodes
+    fl, ops = bench.volume_fp64_cost(4, "rect")
+    assert ops == 9 + 5 * 15 + 5 + 75 / 125
+    assert fl == (3 * 2 + 6) + 5 * (1 + 14 * 2) + 5 + 75 / 125
+    assert bench.volume_fp64_cost(4, "affine")[0] == 30 * 5 + 65
+    assert bench.volume_flops_per_elem_node(4, affine=True) == fl
+    for N in range(1, 9):
+        assert bench.volume_fp64_cost(N, "rect")[1] < bench.volume_fp64_cost(N, "nodal")[1]
 
 
 def test_byte_models():
