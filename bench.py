@@ -269,17 +269,41 @@ def cpu_worker(args):
                       "Ng": m.Ng}))
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (empty if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for ln in out.splitlines():
+        if ln.strip().lower().startswith("model name"):
+            return ln.split(":", 1)[1].strip()
+    return ""
+
+
 def cpu_baseline(args):
-    env = dict(os.environ)
-    env.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", args.workload,
-                        "--cpu-seconds", str(args.cpu_seconds)], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
-            "sample": f"{d['steps']} SSP-RK3 steps ({STAGES * d['steps']} stages) of {args.workload} "
-                      f"on all {d['Ng']} global nodes, {d['seconds']:.1f} s, FP64 C oracle (-O2, OpenMP)"}
+    """The oracle on all host cores (OpenMP), and a short sample on one core."""
+    def run(threads, seconds):
+        env = dict(os.environ)
+        env["OMP_NUM_THREADS"] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", args.workload,
+                            "--cpu-seconds", str(seconds)], capture_output=True, text=True, env=env)
+        if r.returncode != 0:
+            return None, r.stderr.strip().splitlines()[-1] if r.stderr else "failed"
+        return json.loads(r.stdout.strip().splitlines()[-1]), None
+
+    d, err = run(int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), args.cpu_seconds)
+    if d is None:
+        return {"error": err}
+    out = {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+           "sample": f"{d['steps']} SSP-RK3 steps ({STAGES * d['steps']} stages) of {args.workload} "
+                     f"on all {d['Ng']} global nodes, {d['seconds']:.1f} s, FP64 C oracle (-O2, OpenMP)",
+           "cpu_model": cpu_model()}
+    one, _ = run(1, 0.0)  # one warm-up step, then one timed step
+    if one is not None:
+        out["one_core"] = {"value": one["value"], "unit": UNIT,
+                           "sample": f"{one['steps']} SSP-RK3 step(s), {one['seconds']:.1f} s, one thread"}
+    return out
 
 
 def run_reference(args):
