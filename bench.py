@@ -123,10 +123,10 @@ def volume_fp64_cost(N: int, form: str) -> tuple:
       9 + 36 (N+1) + 45 operations, 72 (N+1) + 107 flops.
     - "rect", rectilinear affine elements: the same 12 fields; per equation
       three contractions of length N+1 with K_d D (3 (N+1) operations, the
-      first a product: 6 (N+1) - 1 flops) and one product by w_i w_j w_k;
-      the element's K_d D, 3 (N+1)^2 products shared by its (N+1)^3 nodes:
-      14 + 15 (N+1) + 3 / (N+1) operations, 12 + 5 (6 (N+1) - 1) + 5 +
-      3 / (N+1) flops.
+      first a product: 6 (N+1) - 1 flops); the weight w_i w_j w_k goes with
+      the inverse mass into the update; the element's K_d D, 3 (N+1)^2
+      products shared by its (N+1)^3 nodes: 9 + 15 (N+1) + 3 / (N+1)
+      operations, 12 + 5 (6 (N+1) - 1) + 3 / (N+1) flops.
     - "affine", affine elements with a full metric: per direction B_d.u and
       B_d.U (3 operations, 5 flops each), three momentum fluxes
       U_c (B_d.u) + B_dc p' (2 operations, 3 flops each) and theta (B_d.U)
@@ -134,7 +134,7 @@ def volume_fp64_cost(N: int, form: str) -> tuple:
       44 + 15 (N+1) operations, 30 (N+1) + 65 flops."""
     P = N + 1
     if form == "rect":
-        return 12.0 + 5.0 * (6 * P - 1) + 5.0 + 3.0 / P, 14.0 + 15.0 * P + 3.0 / P
+        return 12.0 + 5.0 * (6 * P - 1) + 3.0 / P, 9.0 + 15.0 * P + 3.0 / P
     if form == "affine":
         return 30.0 * P + 65.0, 44.0 + 15.0 * P
     return 72.0 * P + 107.0, 9.0 + 36.0 * P + 45.0

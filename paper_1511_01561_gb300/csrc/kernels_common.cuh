@@ -396,8 +396,13 @@ __host__ __device__ constexpr int line_group() {
 //     element, so -Jw div F at node (i,j,k) is w_i w_j w_k sum_d K_d (D F_d)
 //     along xi_d, with K_d = -J dxi_d/dx_d per element.  Folding K_d into the
 //     direction's copy of D (formed per element in shared memory) leaves the
-//     12 unweighted flux fields of (1), 15 contractions and one product by
-//     w_i w_j w_k per equation, with no metric or Jw load per node.
+//     12 unweighted flux fields of (1) and 15 contractions, with no metric or
+//     Jw load per node.  The weight w_i w_j w_k is the same at every element
+//     node of a global node (the Lobatto weights are symmetric and the box's
+//     elements meet face to face), so it moves out of the element kernel
+//     into the inverse mass of the DSS: the kernel writes
+//     sum_d K_d (D F_d), and the update multiplies the sum over element
+//     nodes by w_i w_j w_k / M (Minv_r) instead of 1 / M.
 
 // Flux fields of the FP64 per-node kernel: F_U = U (x) u + p' I with the
 // pressure in the diagonal components (the symmetric part stored once).
@@ -490,9 +495,10 @@ __device__ __forceinline__ void volume_element_nodal64(const VolumeArgs& a, long
 }
 
 // create_rhs of a rectilinear affine element in FP64 (see (2) above), one
-// thread per element node: 9 + 75 + 5 FP64 operations per node at N = 4.
-// a.affk holds K_d per element [3][Ne], a.w3_64 the weights w_i w_j w_k
-// [(N+1)^3].  Shared memory: 12 (N+1)^3 + 3 (N+1)^2 doubles.
+// thread per element node: 9 + 75 FP64 operations per node at N = 4.  It
+// writes the residual without its weight w_i w_j w_k, which the update
+// applies with the inverse mass.  a.affk holds K_d per element [3][Ne].
+// Shared memory: 12 (N+1)^3 + 3 (N+1)^2 doubles.
 template <int N>
 __device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
   constexpr int P = N + 1, PP = P * P, NP = PP * P;
@@ -530,8 +536,7 @@ __device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long lo
     dz[m] = Dk[2 * PP + k * P + m];
   }
   const int bx = P * (j + P * k), by = i + PP * k, bz = i + P * j;
-  const double w3 = a.w3_64[l];
-  // w_i w_j w_k (K_x D F_x along xi + K_y D F_y along eta + K_z D F_z along zeta)
+  // K_x D F_x along xi + K_y D F_y along eta + K_z D F_z along zeta
   auto div = [&](int fx, int fy, int fz) {
     const double* gx = F + fx * NP;
     const double* gy = F + fy * NP;
@@ -543,7 +548,7 @@ __device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long lo
     for (int m = 0; m < P; ++m) t = fma(dy[m], gy[by + P * m], t);
 #pragma unroll
     for (int m = 0; m < P; ++m) t = fma(dz[m], gz[bz + PP * m], t);
-    return w3 * t;
+    return t;
   };
   double* re = static_cast<double*>(a.re);
   re[n] = div(lUx, lUy, lUz);
@@ -914,9 +919,9 @@ __device__ __forceinline__ void volume_element_pairs_affine(const VolumeArgs& a,
 }
 
 // create_rhs of a rectilinear affine element in the pairs mode: the folded
-// form of volume_element_rect (K_d D per direction, one product by
-// w_i w_j w_k per equation, no metric or Jw per node) in (hi, lo) float
-// pairs.  The 12 unweighted fields are differentiated less their values at
+// form of volume_element_rect (K_d D per direction, the weight w_i w_j w_k
+// left to the update's inverse mass, no metric or Jw per node) in (hi, lo)
+// float pairs.  The 12 unweighted fields are differentiated less their values at
 // element node 0 (K_d D annihilates constants as D does), and p' enters less
 // its node-0 value (as in volume_element_pairs_affine).  smem_raw holds
 // 12 (N+1)^3 + 3 (N+1)^2 + 12 pairs.
@@ -969,7 +974,6 @@ __device__ __forceinline__ void volume_element_pairs_rect(const VolumeArgs& a, l
   if (l >= NP) return;
   const int i = l % P, j = (l / P) % P, k = l / PP;
   const int bx = P * (j + P * k), by = i + PP * k, bz = i + P * j;
-  const Pairs w3 = split64(a.w3_64[l]);
   double* re = static_cast<double*>(a.re);
   auto div = [&](int fx, int fy, int fz) {
     const Pairs* gx = F + fx * NP;
@@ -983,7 +987,7 @@ __device__ __forceinline__ void volume_element_pairs_rect(const VolumeArgs& a, l
     for (int m = 0; m < P; ++m) pp_fma(h, lo, Dk[PP + j * P + m], gy[by + P * m]);
 #pragma unroll
     for (int m = 0; m < P; ++m) pp_fma(h, lo, Dk[2 * PP + k * P + m], gz[bz + PP * m]);
-    return join64(pp_mul(w3, pp_norm(h, lo)));
+    return join64(pp_norm(h, lo));
   };
   re[n] = div(lUx, lUy, lUz);
   re[Nl + n] = div(lTxx, lTxy, lTxz);

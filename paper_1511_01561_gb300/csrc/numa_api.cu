@@ -65,7 +65,6 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.D2 = c->L.D2;
   a.re = re;
   a.affk = c->L.affk;
-  a.w3_64 = c->L.w3_64;
   a.Ng = c->mesh.Ng;
   a.Nl = c->mesh.Nl;
   a.Ne = (int)c->mesh.Ne;
@@ -82,7 +81,9 @@ UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, cons
   a.idx = c->L.csr_idx;
   a.order = c->L.dss_order;
   a.re = re;
-  a.Minv = c->L.Minv;
+  // the rectilinear element kernels leave out the w_i w_j w_k weight, which
+  // Minv_r carries; the filter's correction (mode 3) is Jw-weighted
+  a.Minv = (mode != 3 && c->rect) ? c->L.Minv_r : c->L.Minv;
   a.wall = c->L.wall;
   a.gvec = c->L.gvec;
   a.nrm = c->L.nrm;
@@ -465,7 +466,7 @@ size_t layout_workspace(const numa_config& c, const HostMesh& m, char* base, Dev
   d.D64 = (double*)take(PP * 8);
   if ((c.precision == NUMA_FP64 || c.precision == NUMA_FP64_PAIRS) && affine_elements(c)) {
     d.affk = (double*)take(3 * (size_t)m.Ne * 8);
-    d.w3_64 = (double*)take(PP * m.P * 8);
+    d.Minv_r = (double*)take(Ng * 8);
   }
   d.D32 = (float*)take(PP * 4);
   d.D2 = (float2*)take(PP * 8);
@@ -612,7 +613,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
   // FP64: the weighted metric of the per-node form; FP64 and pairs: the
   // per-element constants of rectilinear elements
-  std::vector<double> affk, w3;
+  std::vector<double> affk, w3, Minv_r;
   bool rect = false;
   if (c->cfg.precision == NUMA_FP64 || c->cfg.precision == NUMA_FP64_PAIRS) {
     if (!affine_elements(c->cfg)) {
@@ -633,8 +634,22 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
       for (int k = 0; k < P; ++k)
         for (int j = 0; j < P; ++j)
           for (int i = 0; i < P; ++i) w3[i + P * (j + P * k)] = m.w[i] * m.w[j] * m.w[k];
+      // Minv_r: w_i w_j w_k of the node's first element node (its DSS list
+      // is ascending), times 1/M.  Lobatto weights are symmetric, so every
+      // element node of a global node of a box has that weight; a mesh
+      // where they differ keeps the general affine form.
+      if (rect) {
+        const long long Np = m.Np;
+        Minv_r.resize((size_t)Ng);
+        for (size_t I = 0; I < Ng && rect; ++I) {
+          const double wf = w3[m.csr_idx[m.csr_off[I]] % Np];
+          for (int32_t t = m.csr_off[I] + 1; t < m.csr_off[I + 1]; ++t)
+            if (std::fabs(w3[m.csr_idx[t] % Np] - wf) > 1e-14 * wf) rect = false;
+          Minv_r[I] = wf * m.Minv[I];
+        }
+      }
       up(L.affk, affk.data(), affk.size() * 8);
-      up(L.w3_64, w3.data(), w3.size() * 8);
+      if (rect) up(L.Minv_r, Minv_r.data(), Minv_r.size() * 8);
     }
   }
   up(L.l2g, m.l2g.data(), Nl * 4);

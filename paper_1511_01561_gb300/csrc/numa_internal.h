@@ -72,12 +72,13 @@ struct DevLayout {
   uint8_t* dss_order = nullptr;  // [ceil(Ng/kDssBlock)*kDssBlock]
   double* ref = nullptr;     // [4][Ng]
   double* Minv = nullptr;    // [Ng]
+  double* Minv_r = nullptr;  // rectilinear form (FP64, pairs): [Ng] w_i w_j w_k / M, the weight of the node's
+                             // element nodes (equal at all of them) folded into the inverse mass
   uint8_t* wall = nullptr;   // [Ng]
   double* gvec = nullptr;    // [3][Ng] (shell)
   double* nrm = nullptr;     // [3][Ng] (shell)
   double* D64 = nullptr;     // [P*P]
   double* affk = nullptr;    // FP64 / pairs affine elements: [3][Ne] K_d = -J dxi_d/dx_d per element
-  double* w3_64 = nullptr;   // FP64 / pairs affine elements: [P^3] w_i w_j w_k at local node i + P (j + P k)
   float* D32 = nullptr;      // [P*P]
   double* F64 = nullptr;     // [P*P] 1D filter matrix (FP64, pairs)
   float* F32 = nullptr;      // [P*P] the same in FP32 (FP32 form)
@@ -120,7 +121,6 @@ struct VolumeArgs {
   const float2* D2;    // pairs mode
   void* re;            // [5][Nl] output
   const double* affk;   // rectilinear form (FP64, pairs): [3][Ne] -J dxi_d/dx_d
-  const double* w3_64;  // rectilinear form: [P^3] w_i w_j w_k
   long long Ng, Nl;
   int Ne;
   int ebeg, ecnt;      // the launch covers elements [ebeg, ebeg + ecnt) (a slab, or all: 0, Ne)

@@ -18,12 +18,12 @@ def test_flop_models():
     # terms, 15 chain-rule triples (the kernel's "9 + 180 + 45")
     fl, ops = bench.volume_fp64_cost(4, "nodal")
     assert ops == 9 + 12 * 3 * 5 + 15 * 3 and fl == 72 * 5 + 107
-    # rectilinear form at N=4: 9 flux operations (3 FMAs, 6 products), 5
-    # equations x 15 terms (the first a product) and one weight product,
-    # K_d D: 75 products per 125 nodes
+    # rectilinear form at N=4: 9 flux operations (3 FMAs, 6 products) and 5
+    # equations x 15 terms (the first a product); K_d D: 75 products per
+    # 125 nodes (the weight w_i w_j w_k is applied in the update)
     fl, ops = bench.volume_fp64_cost(4, "rect")
-    assert ops == 9 + 5 * 15 + 5 + 75 / 125
-    assert fl == (3 * 2 + 6) + 5 * (1 + 14 * 2) + 5 + 75 / 125
+    assert ops == 9 + 5 * 15 + 75 / 125
+    assert fl == (3 * 2 + 6) + 5 * (1 + 14 * 2) + 75 / 125
     assert bench.volume_fp64_cost(4, "affine")[0] == 30 * 5 + 65
     assert bench.volume_flops_per_elem_node(4, affine=True) == fl
     for N in range(1, 9):
