@@ -115,29 +115,26 @@ def volume_fp64_cost(N: int, form: str) -> tuple:
     """(flops, FP64 operations) per element node of the FP64 element kernel
     of `form`.  A flop count takes an FMA as 2; an operation count takes an
     FMA, a product and a sum as 1 each (each takes one slot of the FP64 pipe).
-    - "nodal", the per-node form of Eq. 5 (any element): 12 flux fields
-      (U, the symmetric U (x) u + p' I, theta U: 9 operations, 12 flops),
-      each differentiated along xi, eta and zeta (3 (N+1) operations,
-      6 (N+1) - 3 flops), and 15 uses of a derivative triple folded into
-      their equations with the -Jw-weighted metric (3 operations, 6 flops):
-      9 + 36 (N+1) + 45 operations, 72 (N+1) + 107 flops.
-    - "rect", rectilinear affine elements: the same 12 fields; per equation
-      three contractions of length N+1 with K_d D (3 (N+1) operations, the
-      first a product: 6 (N+1) - 1 flops); the weight w_i w_j w_k goes with
-      the inverse mass into the update; the element's K_d D, 3 (N+1)^2
-      products shared by its (N+1)^3 nodes: 9 + 15 (N+1) + 3 / (N+1)
-      operations, 12 + 5 (6 (N+1) - 1) + 3 / (N+1) flops.
-    - "affine", affine elements with a full metric: per direction B_d.u and
-      B_d.U (3 operations, 5 flops each), three momentum fluxes
-      U_c (B_d.u) + B_dc p' (2 operations, 3 flops each) and theta (B_d.U)
-      (1), then 15 contractions of length N+1 and 5 products with -Jw:
-      44 + 15 (N+1) operations, 30 (N+1) + 65 flops."""
+    The 12 flux fields (U, the symmetric U (x) u + p' I, theta U) come
+    gathered: the update forms them once per global node.
+    - "nodal", the per-node form of Eq. 5 (any element): each field
+      differentiated along xi, eta and zeta (3 (N+1) operations, 6 (N+1) - 3
+      flops), and 15 uses of a derivative triple folded into their equations
+      with the -Jw-weighted metric (3 operations; 6 flops, 5 for the first
+      use in each of the 5 equations): 36 (N+1) + 45 operations,
+      72 (N+1) + 49 flops.
+    - "rect", rectilinear affine elements: per equation three contractions
+      of length N+1 with K_d D (3 (N+1) operations, the first a product:
+      6 (N+1) - 1 flops); the weight w_i w_j w_k goes with the inverse mass
+      into the update; the element's K_d D, 3 (N+1)^2 products shared by its
+      (N+1)^3 nodes: 15 (N+1) + 3 / (N+1) operations, 5 (6 (N+1) - 1) +
+      3 / (N+1) flops.
+    Affine meshes whose elements are not rectilinear take the per-node
+    form in FP64."""
     P = N + 1
     if form == "rect":
-        return 12.0 + 5.0 * (6 * P - 1) + 3.0 / P, 9.0 + 15.0 * P + 3.0 / P
-    if form == "affine":
-        return 30.0 * P + 65.0, 44.0 + 15.0 * P
-    return 72.0 * P + 107.0, 9.0 + 36.0 * P + 45.0
+        return 5.0 * (6 * P - 1) + 3.0 / P, 15.0 * P + 3.0 / P
+    return 72.0 * P + 49.0, 36.0 * P + 45.0
 
 
 def volume_flops_per_elem_node(N: int, affine: bool = False) -> float:
@@ -153,26 +150,28 @@ def filter_flops_per_elem_node(N: int) -> float:
     return 30.0 * (N + 1) + 10.0
 
 
-def volume_bytes(Nl: int, Ng: int, fp: int, N: int = 4, affine: bool = False) -> float:
-    """Algorithmic DRAM bytes of one volume-kernel launch (fp = 8 for FP64, 4
-    for the FP32-mixed form): metric terms and Jw (10 values per element
-    node; affine elements: Jw per node and 9 metric terms per element), l2g
-    (4 B), the residual write (5 values), and one read per global node of the
-    gathered fields (FP64: U and u, theta, p' = 8 doubles; FP32: 8 floats)."""
+def volume_bytes(Nl: int, Ng: int, fp: int, N: int = 4, affine: bool = False, gathered: int = 8) -> float:
+    """Algorithmic DRAM bytes of one volume-kernel launch (fp = 8 for FP64 and
+    the pairs mode, 4 for the FP32-mixed form): metric terms and Jw (10
+    values per element node; affine elements: Jw per node and 9 metric terms
+    per element), l2g (4 B), the residual write (5 values), and one read per
+    global node of the `gathered` values (FP64: U and the nine flux
+    components, 12; pairs: U and u, theta, p' as pairs, 8; FP32: 8 floats)."""
     if affine:
-        return Nl * (fp + 4 + 5 * fp) + Nl // (N + 1) ** 3 * 9 * fp + Ng * 8 * fp
-    return Nl * (10 * fp + 4 + 5 * fp) + Ng * 8 * fp
+        return Nl * (fp + 4 + 5 * fp) + Nl // (N + 1) ** 3 * 9 * fp + Ng * gathered * fp
+    return Nl * (10 * fp + 4 + 5 * fp) + Ng * gathered * fp
 
 
-def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float, entries: int = None) -> float:
+def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float, entries: int = None, prim: int = None) -> float:
     """Algorithmic DRAM bytes of one DSS/update launch: CSR (4 B per entry +
     4 B per node; `entries` = Nl unless given), residual read (5 values per
     element node, once), M^-1, wall flag, q^k read, q^{k+1} write, q^n on the
     stages that use it, the reference state (4 doubles) and the
-    primitive-field write (40 or 32 B)."""
+    primitive-field write (`prim` bytes: 72 in FP64, 32 in FP32-mixed)."""
     entries = Nl if entries is None else entries
+    prim = (72 if fp == 8 else 32) if prim is None else prim
     return (entries * 4 + Nl * 5 * fp
-            + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + (40 if fp == 8 else 32)))
+            + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + prim))
 
 
 def max_over_ranks(dist, x: float, device=None) -> float:
@@ -477,7 +476,7 @@ def run_mine(args):
                      "traffic": ncu_traffic(f"volume_fp64_{form_name}", args.workload),
                      "algorithmic_flops": flops, "fp64_ops_per_element_node": ops_el,
                      "fp64_pipe_frac": pipe_frac,
-                     "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine),
+                     "algorithmic_bytes": volume_bytes(Nl, Ng, 8, N, affine, gathered=12),
                      "peak_source": FP64_PEAK_SOURCE,
                      "avg_launch_ms": 1e3 * vol_avg_s,
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},

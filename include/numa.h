@@ -179,9 +179,10 @@ int numa_rhs(numa_ctx* ctx, const double* q_dev, double* r_dev);
  * in a fixed 16 MiB device array inside the library
  * (NUMA_STATIC_SCRATCH_BYTES) instead of the bound workspace, and nothing is
  * allocated: no cudaMalloc, no cudaFree, no allocating library call.
- * Scratch per global node: 40 bytes (FP64), 32 (FP32-mixed), 64 (pairs); per
+ * Scratch per global node: 72 bytes (FP64), 32 (FP32-mixed), 64 (pairs); per
  * element node: 40 (FP64, pairs) or 20 (FP32-mixed).  At N=4 the largest
- * cubic boxes that fit are 12^3 elements (FP64, pairs) and 15^3 (FP32-mixed);
+ * cubic boxes that fit are 11^3 elements (FP64), 12^3 (pairs) and 15^3
+ * (FP32-mixed);
  * larger meshes return NUMA_EINVAL with the bytes needed in
  * numa_last_error.  The first call in each CUDA context (normally one per
  * device) looks up the array's device address and caches it; make that first

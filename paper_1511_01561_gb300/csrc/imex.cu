@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kImexThreads) imex_column_kernel(ImexArgs a) {
     a.q[3 * Ng + g] = xz;
     a.qs[3 * Ng + g] = fma(nu, xz, a.qs[3 * Ng + g]);
     if (nonfinite(xr) | nonfinite(xu) | nonfinite(xv) | nonfinite(xz) | nonfinite(xt)) atomicOr(a.flag, 1);
-    write_prim(a.pa, g, xr, xu, xv, xz, xt);
+    write_prim<false>(a.pa, g, xr, xu, xv, xz, xt);  // FP64 or pairs
   }
 }
 

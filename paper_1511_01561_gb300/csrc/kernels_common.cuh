@@ -182,12 +182,16 @@ __device__ __forceinline__ double eos_ratio(double x, const PrimArgs& a) {
 
 // Primitive fields of state (rp, U, Tp) at global node I (reference from a.ref):
 // rho = rho0 + rho', u = U / rho, theta = (Theta0 + Theta') / rho,
-// p' = p0 ((1 + Theta'/Theta0)^gamma - 1).
+// p' = p0 ((1 + Theta'/Theta0)^gamma - 1); in FP64 the flux components
+// built from them (the element kernels' gathered input).
+// F32: the FP32-mixed form (known at compile time, so that its kernels carry
+// none of the FP64 form's code); otherwise FP64 or pairs by a.precision.
+template <bool F32>
 __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, double rp, double Ux, double Uy,
                                            double Uz, double Tp) {
   const long long Ng = a.Ng;
   const double rho0 = a.ref[I], Th0 = a.ref[Ng + I], p0 = a.ref[2 * Ng + I], iTh0 = a.ref[3 * Ng + I];
-  if (a.precision == NUMA_FP32_MIXED) {
+  if constexpr (F32) {
     // u and theta are FP32 fields, so rho and Theta are summed in FP32; p'
     // (the reference-state subtraction of the equation of state) in FP64, to
     // the accuracy of the float it is stored as
@@ -198,7 +202,7 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     w[2 * I] = make_float4(Uxf, Uyf, Uzf, Uxf * rf);
     w[2 * I + 1] = make_float4(Uyf * rf, Uzf * rf, (d2f(Th0) + d2f(Tp)) * rf, d2f(p0 * eos_ratio<true>(Tp * iTh0, a)));
     return;
-  }
+  } else {
   const double rho = rho0 + rp;
   const double Th = Th0 + Tp;
   if (a.precision == NUMA_FP64_PAIRS) {
@@ -214,13 +218,23 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
     w[6 * Ng + I] = split64(Th * r);
     w[7 * Ng + I] = split64(p0 * eos_ratio(Tp * iTh0, a));
   } else {
+    // FP64: the nine flux components the element kernels need besides U,
+    // formed once per global node (kFlux64 slots): U_c u_c + p' on the
+    // diagonal, the symmetric U_c u_d once, and theta U = Theta u
     double* w = static_cast<double*>(a.prim);
     const double r = rcp64(rho);
-    w[I] = Ux * r;
-    w[Ng + I] = Uy * r;
-    w[2 * Ng + I] = Uz * r;
-    w[3 * Ng + I] = Th * r;
-    w[4 * Ng + I] = p0 * eos_ratio(Tp * iTh0, a);
+    const double ux = Ux * r, uy = Uy * r, uz = Uz * r;
+    const double pp = p0 * eos_ratio(Tp * iTh0, a);
+    w[I] = fma(Ux, ux, pp);
+    w[Ng + I] = fma(Uy, uy, pp);
+    w[2 * Ng + I] = fma(Uz, uz, pp);
+    w[3 * Ng + I] = Ux * uy;
+    w[4 * Ng + I] = Ux * uz;
+    w[5 * Ng + I] = Uy * uz;
+    w[6 * Ng + I] = Th * ux;
+    w[7 * Ng + I] = Th * uy;
+    w[8 * Ng + I] = Th * uz;
+  }
   }
 }
 
@@ -229,7 +243,7 @@ __device__ __forceinline__ void write_prim(const PrimArgs& a, long long I, doubl
 enum : int { kUx = 0, kUy, kUz, kTxx, kTxy, kTxz, kTyy, kTyz, kTzz, kPp, kHx, kHy, kHz, kNF };
 
 // Momentum and primitive fields of the global node behind element node n
-// (CG storage: gathered through l2g).
+// (CG storage: gathered through l2g), FP32 form.
 template <typename T>
 struct NodeState {
   T Ux, Uy, Uz, ux, uy, uz, th, pp;
@@ -237,20 +251,10 @@ struct NodeState {
 
 template <typename T>
 __device__ __forceinline__ NodeState<T> gather_node(const VolumeArgs& a, long long n) {
-  const long long Ng = a.Ng;
+  static_assert(sizeof(T) == 4, "the FP64 kernels gather flux components (gather_fluxes64)");
   const int g = a.l2g[n];
   NodeState<T> z;
-  if constexpr (sizeof(T) == 8) {
-    const double* w = static_cast<const double*>(a.prim);
-    z.Ux = a.q[Ng + g];
-    z.Uy = a.q[2 * Ng + g];
-    z.Uz = a.q[3 * Ng + g];
-    z.ux = w[g];
-    z.uy = w[Ng + g];
-    z.uz = w[2 * Ng + g];
-    z.th = w[3 * Ng + g];
-    z.pp = w[4 * Ng + g];
-  } else {
+  {
     const float4* w = static_cast<const float4*>(a.prim);
     const float4 p = w[2 * g], r = w[2 * g + 1];
     z.Ux = p.x;
@@ -313,55 +317,35 @@ __device__ __forceinline__ void stage_fluxes_affine(const VolumeArgs& a, long lo
   }
 }
 
-// create_rhs of an affine element (see stage_fluxes_affine), one thread per
-// element node: each equation's divergence is three contractions with D of
-// the staged contravariant fluxes, 15 per node instead of 39.  The element's
-// metric terms are read at its first node.  smem_raw holds 15 (N+1)^3 +
-// (N+1)^2 values of T.
-template <int N, typename T>
-__device__ __forceinline__ void volume_element_affine(const VolumeArgs& a, long long e, unsigned char* smem_raw) {
-  constexpr int P = N + 1, NP = P * P * P;
-  T* G = reinterpret_cast<T*>(smem_raw);  // [15][NP]
-  T* Ds = G + 15 * NP;                      // [P][P]
-  const T* Dg = reinterpret_cast<const T*>(a.D64);
-  const T* met = reinterpret_cast<const T*>(a.met64);
-  static_assert(sizeof(T) == 8, "FP64 form");
-  const int l = threadIdx.x;
-  for (int t = l; t < P * P; t += blockDim.x) Ds[t] = Dg[t];
-  const long long Nl = a.Nl, e0 = (long long)e * NP, n = e0 + l;
-  if (l < NP) {
-    T B[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + e0];
-    stage_fluxes_affine<N, T>(a, n, l, B, G);
-  }
-  __syncthreads();
-  if (l >= NP) return;
-  const int i = l % P, j = (l / P) % P, k = l / (P * P);
-  T dx[P], dy[P], dz[P];
-#pragma unroll
-  for (int m = 0; m < P; ++m) {
-    dx[m] = Ds[i * P + m];
-    dy[m] = Ds[j * P + m];
-    dz[m] = Ds[k * P + m];
-  }
-  const T jw = met[9 * Nl + n];
-  const int bx = P * (j + P * k), by = i + P * P * k, bz = i + P * j;
-  T* re = static_cast<T*>(a.re);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const T* g0 = G + (3 * v) * NP;
-    const T* g1 = g0 + NP;
-    const T* g2 = g1 + NP;
-    T t = T(0);
-#pragma unroll
-    for (int m = 0; m < P; ++m) t = fma(dx[m], g0[bx + m], t);
-#pragma unroll
-    for (int m = 0; m < P; ++m) t = fma(dy[m], g1[by + P * m], t);
-#pragma unroll
-    for (int m = 0; m < P; ++m) t = fma(dz[m], g2[bz + P * P * m], t);
-    re[v * Nl + n] = -(jw * t);
-  }
+// The 12 flux fields of the FP64 (and pairs) kernels: F_rho = U, F_U =
+// U (x) u + p' I with the pressure in the diagonal components (the
+// symmetric part stored once), F_Theta = theta U.
+enum : int { lUx = 0, lUy, lUz, lTxx, lTyy, lTzz, lTxy, lTxz, lTyz, lHx, lHy, lHz, kLF };
+
+// The 12 flux fields at the global node behind element node n, FP64: U from
+// the state, the other nine as the update kernel formed them (write_prim).
+struct FluxState64 {
+  double f[kLF];
+};
+
+__device__ __forceinline__ FluxState64 gather_fluxes64(const VolumeArgs& a, long long n) {
+  const long long Ng = a.Ng;
+  const int g = a.l2g[n];
+  const double* w = static_cast<const double*>(a.prim);
+  FluxState64 z;
+  z.f[lUx] = a.q[Ng + g];
+  z.f[lUy] = a.q[2 * Ng + g];
+  z.f[lUz] = a.q[3 * Ng + g];
+  z.f[lTxx] = w[g];
+  z.f[lTyy] = w[Ng + g];
+  z.f[lTzz] = w[2 * Ng + g];
+  z.f[lTxy] = w[3 * Ng + g];
+  z.f[lTxz] = w[4 * Ng + g];
+  z.f[lTyz] = w[5 * Ng + g];
+  z.f[lHx] = w[6 * Ng + g];
+  z.f[lHy] = w[7 * Ng + g];
+  z.f[lHz] = w[8 * Ng + g];
+  return z;
 }
 
 // D of every order N = 1..8 in FP32 ([N][(N+1)^2], row-major), read by the
@@ -404,9 +388,6 @@ __host__ __device__ constexpr int line_group() {
 //     sum_d K_d (D F_d), and the update multiplies the sum over element
 //     nodes by w_i w_j w_k / M (Minv_r) instead of 1 / M.
 
-// Flux fields of the FP64 per-node kernel: F_U = U (x) u + p' I with the
-// pressure in the diagonal components (the symmetric part stored once).
-enum : int { lUx = 0, lUy, lUz, lTxx, lTyy, lTzz, lTxy, lTxz, lTyz, lHx, lHy, lHz, kLF };
 
 // create_rhs of element e in FP64, per-node form of Eq. 5 (any element,
 // curved included), one thread per element node.  The metric terms arrive
@@ -414,7 +395,8 @@ enum : int { lUx = 0, lUy, lUz, lTxx, lTyy, lTzz, lTxy, lTxz, lTyz, lHx, lHy, lH
 // form), and the pressure sits in the diagonal momentum fluxes, so each of
 // the 12 staged flux fields (kLF) is differentiated along xi, eta and zeta
 // (15 FMAs) and folded into the divergence of every equation that uses it
-// with three FMAs: 9 + 180 + 45 FP64 operations per node at N = 4.  The
+// with three FMAs: 180 + 45 FP64 operations per node at N = 4 (the update
+// formed the flux components once per global node).  The
 // result is the weighted residual -Jw div F of Eq. 4.  smem_raw holds
 // 12 (N+1)^3 + (N+1)^2 doubles.
 template <int N>
@@ -430,19 +412,9 @@ __device__ __forceinline__ void volume_element_nodal64(const VolumeArgs& a, long
   if (l < NP) {
 #pragma unroll
     for (int t = 0; t < 9; ++t) B[t] = met[t * Nl + n];
-    const NodeState<double> z = gather_node<double>(a, n);
-    F[lUx * NP + l] = z.Ux;
-    F[lUy * NP + l] = z.Uy;
-    F[lUz * NP + l] = z.Uz;
-    F[lTxx * NP + l] = fma(z.Ux, z.ux, z.pp);
-    F[lTyy * NP + l] = fma(z.Uy, z.uy, z.pp);
-    F[lTzz * NP + l] = fma(z.Uz, z.uz, z.pp);
-    F[lTxy * NP + l] = z.Ux * z.uy;
-    F[lTxz * NP + l] = z.Ux * z.uz;
-    F[lTyz * NP + l] = z.Uy * z.uz;
-    F[lHx * NP + l] = z.th * z.Ux;
-    F[lHy * NP + l] = z.th * z.Uy;
-    F[lHz * NP + l] = z.th * z.Uz;
+    const FluxState64 z = gather_fluxes64(a, n);
+#pragma unroll
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = z.f[f];
   }
   __syncthreads();
   if (l >= NP) return;
@@ -495,7 +467,8 @@ __device__ __forceinline__ void volume_element_nodal64(const VolumeArgs& a, long
 }
 
 // create_rhs of a rectilinear affine element in FP64 (see (2) above), one
-// thread per element node: 9 + 75 FP64 operations per node at N = 4.  It
+// thread per element node: 75 FP64 operations per node at N = 4 (the flux
+// components come from the update, formed once per global node).  It
 // writes the residual without its weight w_i w_j w_k, which the update
 // applies with the inverse mass.  a.affk holds K_d per element [3][Ne].
 // Shared memory: 12 (N+1)^3 + 3 (N+1)^2 doubles.
@@ -511,19 +484,9 @@ __device__ __forceinline__ void volume_element_rect(const VolumeArgs& a, long lo
   }
   const long long Nl = a.Nl, n = (long long)e * NP + l;
   if (l < NP) {
-    const NodeState<double> z = gather_node<double>(a, n);
-    F[lUx * NP + l] = z.Ux;
-    F[lUy * NP + l] = z.Uy;
-    F[lUz * NP + l] = z.Uz;
-    F[lTxx * NP + l] = fma(z.Ux, z.ux, z.pp);
-    F[lTyy * NP + l] = fma(z.Uy, z.uy, z.pp);
-    F[lTzz * NP + l] = fma(z.Uz, z.uz, z.pp);
-    F[lTxy * NP + l] = z.Ux * z.uy;
-    F[lTxz * NP + l] = z.Ux * z.uz;
-    F[lTyz * NP + l] = z.Uy * z.uz;
-    F[lHx * NP + l] = z.th * z.Ux;
-    F[lHy * NP + l] = z.th * z.Uy;
-    F[lHz * NP + l] = z.th * z.Uz;
+    const FluxState64 z = gather_fluxes64(a, n);
+#pragma unroll
+    for (int f = 0; f < kLF; ++f) F[f * NP + l] = z.f[f];
   }
   __syncthreads();
   if (l >= NP) return;
@@ -1002,7 +965,7 @@ template <int N, typename T, bool AFF>
 constexpr size_t element_smem_bytes() {
   constexpr int P = N + 1, NP = P * P * P;
   if constexpr (std::is_same<T, float>::value) return sizeof(float) * (kNF > 15 ? kNF : 15) * NP;
-  if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (15 * NP + P * P);
+  if constexpr (AFF && std::is_same<T, double>::value) return sizeof(T) * (kLF * NP + 3 * P * P);
   if constexpr (std::is_same<T, double>::value) return sizeof(T) * (kLF * NP + P * P);
   if constexpr (AFF) return sizeof(T) * (15 * NP + P * P + 15);
   return sizeof(T) * (kLF * NP + P * P + kLF);
@@ -1022,9 +985,9 @@ __device__ __forceinline__ void element_rhs(const VolumeArgs& a, long long e, un
   } else if constexpr (std::is_same<T, float>::value) {
     volume_element_lines<N, AFF>(a, e, smem_raw);
   } else if constexpr (AFF) {
-    // uniform over the CTA: rectilinear elements take the folded form
-    if (a.affine == 2) volume_element_rect<N>(a, e, smem_raw);
-    else volume_element_affine<N, T>(a, e, smem_raw);
+    // FP64 launches the affine instantiation for rectilinear elements only
+    // (volume_form); other affine meshes take the per-node form
+    volume_element_rect<N>(a, e, smem_raw);
   } else {
     volume_element_nodal64<N>(a, e, smem_raw);
   }
@@ -1150,7 +1113,7 @@ __device__ __forceinline__ void dss_box(const UpdateArgs& a, long long I, double
 }
 
 // Everything after the DSS at global node I, given its sums s0..s4.
-template <int MODE, bool SHELL>
+template <int MODE, bool SHELL, bool F32>
 __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long I, double s0, double s1, double s2,
                                                  double s3, double s4) {
   const long long Ng = a.Ng;
@@ -1180,7 +1143,7 @@ __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long 
     a.out[3 * Ng + I] = y3;
     a.out[4 * Ng + I] = y4;
     if (nonfinite(y0) | nonfinite(y1) | nonfinite(y2) | nonfinite(y3) | nonfinite(y4)) atomicOr(a.flag, 1);
-    write_prim(a.pa, I, y0, y1, y2, y3, y4);
+    write_prim<F32>(a.pa, I, y0, y1, y2, y3, y4);
     return;
   }
   if constexpr (MODE == 0 || MODE >= 4 || SHELL) {
@@ -1236,7 +1199,7 @@ __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long 
       bad |= nonfinite(y[v]);
     }
     if (bad) atomicOr(a.flag, 1);
-    write_prim(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
+    write_prim<F32>(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
   } else if constexpr (MODE >= 1) {
     // q^{k+1} = a q^n + b q^k + b dt R with, in the box, the inverse mass
     // folded into one coefficient: b dt R_v = c s_v (+ b dt S_v), c = b dt / M
@@ -1263,7 +1226,7 @@ __device__ __forceinline__ void update_node_sums(const UpdateArgs& a, long long 
       bad |= nonfinite(y[v]);
     }
     if (bad) atomicOr(a.flag, 1);
-    write_prim(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
+    write_prim<F32>(a.pa, I, y[0], y[1], y[2], y[3], y[4]);
   }
 }
 
@@ -1271,7 +1234,7 @@ template <int MODE, bool SHELL, typename RT>
 __device__ __forceinline__ void update_node(const UpdateArgs& a, long long I) {
   double s[5];
   dss_node<RT>(a, I, s);
-  update_node_sums<MODE, SHELL>(a, I, s[0], s[1], s[2], s[3], s[4]);
+  update_node_sums<MODE, SHELL, std::is_same<RT, float>::value>(a, I, s[0], s[1], s[2], s[3], s[4]);
 }
 
 // One block per kDssBlock consecutive global nodes.  The DSS runs in the
@@ -1298,7 +1261,9 @@ __global__ void __launch_bounds__(kDssBlock) update_kernel(UpdateArgs a) {
   __syncthreads();
   const int t = threadIdx.x;
   const long long I = base + t;
-  if (I < a.iend) update_node_sums<MODE, SHELL>(a, I, sums[0][t], sums[1][t], sums[2][t], sums[3][t], sums[4][t]);
+  if (I < a.iend)
+    update_node_sums<MODE, SHELL, std::is_same<RT, float>::value>(a, I, sums[0][t], sums[1][t], sums[2][t], sums[3][t],
+                                                                  sums[4][t]);
 }
 
 // ---- ragged multi-member kernels (serving) ---------------------------------

@@ -11,11 +11,11 @@
 // buffers with a scratch array that is part of the library image: nothing
 // is allocated per call.
 //
-// The array is 16 MiB.  Per global node the primitive fields take 40 bytes
-// (FP64), 32 (FP32-mixed) or 64 (FP64-pairs); per element node the residuals
-// take 40 (FP64, pairs) or 20 (FP32-mixed).  At N=4 the largest cubic boxes
-// that fit are 12^3 elements in FP64 and in the pairs mode and 15^3 in
-// FP32-mixed.  Every GPU that loads this library keeps the array until the
+// The array is 16 MiB.  Per global node the primitive fields take 72 bytes
+// (FP64: nine flux components), 32 (FP32-mixed) or 64 (FP64-pairs); per
+// element node the residuals take 40 (FP64, pairs) or 20 (FP32-mixed).  At
+// N=4 the largest cubic boxes that fit are 11^3 elements in FP64, 12^3 in
+// the pairs mode and 15^3 in FP32-mixed.  Every GPU that loads this library keeps the array until the
 // process exits.  All calls share it: two calls whose work overlaps on the
 // GPU (different streams, or different contexts on one device) race on it.
 // Nothing in it needs clearing between calls: each call overwrites every

@@ -70,8 +70,17 @@ VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, voi
   a.Ne = (int)c->mesh.Ne;
   a.ebeg = 0;
   a.ecnt = a.Ne;
-  a.affine = affine_elements(c->cfg) ? (c->rect ? 2 : 1) : 0;
+  a.affine = volume_form(c);
   return a;
+}
+
+// Element-kernel form of a bound context: 2 the rectilinear form (FP64,
+// pairs), 1 the general affine form (pairs, FP32-mixed), 0 the per-node form
+// (any element; FP64 takes it on affine elements that are not rectilinear).
+int volume_form(const numa_ctx* c) {
+  if (!affine_elements(c->cfg)) return 0;
+  if (c->rect) return 2;
+  return c->cfg.precision == NUMA_FP64 ? 0 : 1;
 }
 
 UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, const double* qn, double* out,
@@ -611,16 +620,12 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
   up(L.D32, D32.data(), D32.size() * 4);
   up(L.D2, D2.data(), D2.size() * 4);
   if (e == cudaSuccess) e = upload_d32_constant(m.N, D32.data(), s);
-  // FP64: the weighted metric of the per-node form; FP64 and pairs: the
-  // per-element constants of rectilinear elements
+  // FP64 and pairs: the per-element constants of rectilinear elements; FP64:
+  // the weighted metric of the per-node form, which it takes everywhere else
   std::vector<double> affk, w3, Minv_r;
   bool rect = false;
   if (c->cfg.precision == NUMA_FP64 || c->cfg.precision == NUMA_FP64_PAIRS) {
-    if (!affine_elements(c->cfg)) {
-      if (c->cfg.precision == NUMA_FP64 && e == cudaSuccess && Nl)
-        weight_metric_kernel<<<(unsigned)((Nl + 255) / 256), 256, 0, s>>>(L.met64, (long long)Nl);
-      if (e == cudaSuccess) e = cudaGetLastError();
-    } else {
+    if (affine_elements(c->cfg)) {
       const int P = m.P;
       rect = rectilinear_elements(m);
       affk.assign(3 * (size_t)m.Ne, 0.0);
@@ -650,6 +655,11 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
       }
       up(L.affk, affk.data(), affk.size() * 8);
       if (rect) up(L.Minv_r, Minv_r.data(), Minv_r.size() * 8);
+    }
+    if (c->cfg.precision == NUMA_FP64 && !rect) {
+      if (e == cudaSuccess && Nl)
+        weight_metric_kernel<<<(unsigned)((Nl + 255) / 256), 256, 0, s>>>(L.met64, (long long)Nl);
+      if (e == cudaSuccess) e = cudaGetLastError();
     }
   }
   up(L.l2g, m.l2g.data(), Nl * 4);

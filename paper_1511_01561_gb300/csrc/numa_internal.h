@@ -47,12 +47,14 @@ bool init_state_host(const numa_config& c, const HostMesh& m, int kind, const do
 // Per-global-node primitive fields that the volume kernel gathers, written by
 // the stage update (or the primitive pass) for the state the next create_rhs
 // differentiates:
-//   FP64 mode  : double [5][Ng] = u_x, u_y, u_z, theta, p'   (U comes from q)
+//   FP64 mode  : double [9][Ng] = the flux components U_x u_x + p', U_y u_y + p',
+//                U_z u_z + p', U_x u_y, U_x u_z, U_y u_z, Theta u_x, Theta u_y,
+//                Theta u_z (U comes from q), formed once per global node
 //   FP32 mode  : float  [Ng][8] = (U_x, U_y, U_z, u_x), (u_y, u_z, theta, p') per node,
 //                two float4 (one 32-byte sector per node for the gather)
 //   pairs mode : float2 [8][Ng] = the same eight, each as a (hi, lo) pair
 inline int prim_bytes_per_node(int precision) {
-  return precision == NUMA_FP32_MIXED ? 32 : precision == NUMA_FP64_PAIRS ? 64 : 40;
+  return precision == NUMA_FP32_MIXED ? 32 : precision == NUMA_FP64_PAIRS ? 64 : 72;
 }
 
 // Device workspace carved from the caller's buffer.
@@ -124,9 +126,9 @@ struct VolumeArgs {
   long long Ng, Nl;
   int Ne;
   int ebeg, ecnt;      // the launch covers elements [ebeg, ebeg + ecnt) (a slab, or all: 0, Ne)
-  int affine;          // 0: per-node form; 1: every element is affine, the kernel takes the
-                       // contravariant-flux form; 2: every element is also rectilinear (diagonal
-                       // metric terms), FP64 takes the folded form (volume_element_rect)
+  int affine;          // volume_form: 0 the per-node form; 1 every element is affine, the
+                       // contravariant-flux form (FP32-mixed, pairs); 2 every element is also
+                       // rectilinear (diagonal metric terms): the folded form (FP64, pairs)
 };
 
 struct UpdateArgs {
@@ -338,6 +340,7 @@ extern const double kLsB[5];
 
 PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim);
 VolumeArgs volume_args(const numa_ctx* c, const double* q, const void* prim, void* re);
+int volume_form(const numa_ctx* c);
 UpdateArgs update_args(const numa_ctx* c, const void* re, const double* qk, const double* qn, double* out,
                        int mode, double ra, double rb, double dt);
 FilterArgs filter_args(const numa_ctx* c);

@@ -104,7 +104,7 @@ struct Request {
   std::string err;
 };
 
-using GroupKey = std::tuple<int, int, int, int>;  // N, precision, mesh kind, affine elements
+using GroupKey = std::tuple<int, int, int, int>;  // N, precision, mesh kind, element-kernel form (volume_form)
 
 // Workspace bytes of a configuration without building its mesh.
 bool workspace_bytes_of(const numa_config& c, size_t* bytes, long long* Ng) {
@@ -232,7 +232,7 @@ void rebuild_tables(numa_sched* s) {
   for (int g = 0; g < kMaxGroups; ++g) s->h_groups[g].n = 0;
   for (long long id : s->active) {
     Request& r = *s->reqs[id];
-    GroupKey k{r.cfg.N, r.cfg.precision, r.cfg.mesh_kind, affine_elements(r.cfg) ? 1 : 0};
+    GroupKey k{r.cfg.N, r.cfg.precision, r.cfg.mesh_kind, volume_form(r.ctx)};
     auto it = gi.find(k);
     int g;
     if (it == gi.end()) {

@@ -19,7 +19,10 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
   const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= a.Ng) return;
   const long long Ng = a.Ng;
-  write_prim(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
+  if (a.precision == NUMA_FP32_MIXED)
+    write_prim<true>(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
+  else
+    write_prim<false>(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
 }
 
 template <int MODE, typename RT>

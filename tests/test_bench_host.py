@@ -14,18 +14,20 @@ import bench  # noqa: E402
 
 
 def test_flop_models():
-    # per-node form at N=4: 9 flux operations, 12 fields x 3 directions x 5
-    # terms, 15 chain-rule triples (the kernel's "9 + 180 + 45")
+    # the 12 flux fields come gathered (formed once per global node by the
+    # update).  Per-node form at N=4: 12 fields x 3 directions x 5 terms (the
+    # first a product) and 15 chain-rule triples (the first of each of the 5
+    # equations a product and two FMAs)
     fl, ops = bench.volume_fp64_cost(4, "nodal")
-    assert ops == 9 + 12 * 3 * 5 + 15 * 3 and fl == 72 * 5 + 107
-    # rectilinear form at N=4: 9 flux operations (3 FMAs, 6 products) and 5
-    # equations x 15 terms (the first a product); K_d D: 75 products per
-    # 125 nodes (the weight w_i w_j w_k is applied in the update)
+    assert ops == 12 * 3 * 5 + 15 * 3
+    assert fl == 12 * 3 * (1 + 4 * 2) + 5 * (1 + 2 * 2) + 10 * 3 * 2
+    # rectilinear form at N=4: 5 equations x 15 terms (the first a product);
+    # K_d D: 75 products per 125 nodes (the weight w_i w_j w_k is applied in
+    # the update)
     fl, ops = bench.volume_fp64_cost(4, "rect")
-    assert ops == 9 + 5 * 15 + 75 / 125
-    assert fl == (3 * 2 + 6) + 5 * (1 + 14 * 2) + 75 / 125
-    assert bench.volume_fp64_cost(4, "affine")[0] == 30 * 5 + 65
-    assert bench.volume_flops_per_elem_node(4, affine=True) == fl
+    assert ops == 5 * 15 + 75 / 125
+    assert fl == 5 * (1 + 14 * 2) + 75 / 125
+    assert bench.volume_flops_per_elem_node(4, affine=True) == bench.volume_fp64_cost(4, "rect")[0]
     for N in range(1, 9):
         assert bench.volume_fp64_cost(N, "rect")[1] < bench.volume_fp64_cost(N, "nodal")[1]
 
@@ -36,6 +38,10 @@ def test_byte_models():
     assert bench.volume_bytes(Nl, Ng, 8, N, True) == Nl * 52 + Nl // 125 * 72 + Ng * 64
     # per-node form reads all ten metric values at every element node
     assert bench.volume_bytes(Nl, Ng, 8) - bench.volume_bytes(Nl, Ng, 8, N, True) == Nl * 72 - Nl // 125 * 72
+    # FP64 gathers U and the nine flux components (12 doubles per global node)
+    assert bench.volume_bytes(Nl, Ng, 8, N, True, gathered=12) - bench.volume_bytes(Nl, Ng, 8, N, True) == Ng * 32
+    # the FP64 update writes 72 B of flux components per node, FP32-mixed 32 B
+    assert bench.update_bytes(Nl, Ng, 8, 0) - bench.update_bytes(Nl, Ng, 8, 0, prim=32) == Ng * 40
     # the DSS map of CG storage has one entry per element node; DG storage more
     cg = bench.update_bytes(Nl, Ng, 8, 2 / 3)
     assert bench.update_bytes(Nl, Ng, 8, 2 / 3, entries=Nl) == cg

@@ -73,9 +73,9 @@ def test_static_scratch_rejects_meshes_that_do_not_fit(numa):
 
 
 # The largest cubic N=4 box that fits the 16 MiB array in each precision, and
-# the next size up (scratch per global node / per element node: FP64 40 / 40
+# the next size up (scratch per global node / per element node: FP64 72 / 40
 # bytes, FP32-mixed 32 / 20, pairs 64 / 40).
-LIMITS = [("fp64", 12), ("fp32_mixed", 15), ("fp64_pairs", 12)]
+LIMITS = [("fp64", 11), ("fp32_mixed", 15), ("fp64_pairs", 12)]
 
 
 @pytest.mark.parametrize("precision,n", LIMITS)
