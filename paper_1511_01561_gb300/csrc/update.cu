@@ -1,6 +1,7 @@
 // Per-global-node kernels of the GB300 NUMA hot path (sm_103a):
-//   prim_kernel   : the primitive fields (u, theta, p') of a state, which the
-//                   element kernels build their fluxes from;
+//   prim_kernel   : the primitive fields of a state, which the element
+//                   kernels build their fluxes from (FP64: the flux
+//                   components themselves; FP32 and pairs: U, u, theta, p');
 //   update_kernel : deterministic direct stiffness summation over a
 //                   precomputed inverse map (fixed order, no atomics), inverse
 //                   mass matrix, sources, wall condition, the SSP-RK3 stage
