@@ -86,9 +86,9 @@ FP64_PEAK_SOURCE = "nominal FP64 FMA rate; measured 1.258 TFLOP/s (profiles/p0_a
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "6ad946c52a802096", "workload": "bubble_32x32x32_N4",
-               "volume_fp64_affine": 154.801408e6 + 124.720128e6,
-               "volume_pairs_affine": 154.660096e6 + 122.761216e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "99fe37cd8691b993", "workload": "bubble_32x32x32_N4",
+               "volume_fp64_affine": 223.517440e6 + 130.036992e6,
+               "volume_pairs_affine": 154.723840e6 + 123.150848e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
