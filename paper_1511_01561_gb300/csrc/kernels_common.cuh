@@ -79,8 +79,9 @@ struct Pairs {
 };
 
 // double -> pair with integer operations: h = the double's top 24 significant
-// bits (truncated), l = the next bits rounded to a float.  Zeros and values
-// outside float range (below 2^-74 the low part vanishes) take the FP64 path.
+// bits (truncated), l = the next bits rounded to a float.  Values outside
+// float range (below 2^-74 the low part vanishes; zeros excepted) take the
+// FP64 path.
 __device__ __noinline__ Pairs split64_rare(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
@@ -89,6 +90,8 @@ __device__ __noinline__ Pairs split64_rare(double x) {
 __device__ __forceinline__ Pairs split64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const int E = (int)((hi >> 20) & 0x7ffu);  // biased FP64 exponent
+  // zeros (common at walls and in a state at rest) inline, with their sign
+  if (((hi & 0x7fffffffu) | lo) == 0u) return {__uint_as_float(hi & 0x80000000u), 0.0f};
   if (E < 1023 - 74 || E > 1023 + 127) return split64_rare(x);
   const unsigned sign = hi & 0x80000000u;
   const float h = __uint_as_float(sign | ((unsigned)(E - 1023 + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
