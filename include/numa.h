@@ -257,7 +257,7 @@ int numa_set_time_scheme(numa_ctx* ctx, int scheme);
  * both kernels compete for the same pipes and the pipeline measured no gain,
  * so it stays off there); 1 turns the pipeline off; at most 16.  Where a
  * mesh cannot be cut (shells, DG storage, periodic in z, slabs thinner than
- * two node planes, planes of fewer than 256 nodes) one slab is used.  *used
+ * two node planes, planes of fewer than 128 nodes) one slab is used.  *used
  * (may be NULL) receives the slabs in effect (before numa_bind: those that
  * numa_bind will use).  numa_time_kernels always runs unpipelined.  The
  * pipeline creates one CUDA stream and events per context at numa_bind (no

@@ -14,7 +14,7 @@ namespace numa {
 
 constexpr int kMaxN = 8;
 constexpr int kEosTerms = 12;  // binomial-series terms of (1+x)^gamma - 1 for |x| <= 1/32
-constexpr int kDssBlock = 256;  // threads of the update kernel; the DSS order is sorted within such blocks
+constexpr int kDssBlock = 128;  // threads of the update kernel; the DSS order is sorted within such blocks
 
 // Host-side mesh and geometry (Sec. 2.1: Lobatto points, Eq. 4: Jw and M,
 // Eq. 5: isoparametric metric terms).  Built once per context.

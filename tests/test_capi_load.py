@@ -143,7 +143,7 @@ def test_meshes_beyond_32_bit_indices_are_refused(numa):
     (I.box((4, 4, 8), 4), 16, 8),               # at most one slab per element layer
     (I.box((4, 4, 8), 1), 4, 1),                # slabs thinner than two node planes
     (I.box((4, 4, 8), 4, periodic=(0, 0, 1)), 4, 1),  # periodic seam in z
-    (I.box((2, 2, 8), 4), 4, 1),                # planes of fewer than 256 nodes
+    (I.box((2, 2, 8), 4), 4, 1),                # planes of fewer than 128 nodes
     (I.shell(2, 2, 3), 4, 1),
     (dict(I.box((4, 4, 8), 4), storage="dg"), 4, 1),
 ])
