@@ -86,7 +86,7 @@ FP64_PEAK_SOURCE = "nominal FP64 FMA rate; measured 1.258 TFLOP/s (profiles/p0_a
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "e83b7d275b79203f", "workload": "bubble_32x32x32_N4",
+NCU_TRAFFIC = {"kernels_sha256_16": "255ffeb0445a8327", "workload": "bubble_32x32x32_N4",
                "volume_fp64_affine": 223.283200e6 + 131.003648e6,
                "volume_pairs_affine": 154.668032e6 + 122.632192e6,
                "volume_fp32_affine": 139.263488e6 + 49.154048e6}
@@ -94,12 +94,37 @@ NCU_TRAFFIC = {"kernels_sha256_16": "e83b7d275b79203f", "workload": "bubble_32x3
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
 
+def code_lines(text: str) -> list:
+    """The lines of a C/CUDA source with comments and blank lines removed
+    (a `//` inside a string literal stays), stripped of surrounding spaces."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    out = []
+    for ln in text.splitlines():
+        cut = len(ln)
+        start = 0
+        while True:
+            k = ln.find("//", start)
+            if k < 0:
+                break
+            if ln.count('"', 0, k) % 2 == 0:
+                cut = k
+                break
+            start = k + 2
+        ln = ln[:cut].strip()
+        if ln:
+            out.append(ln)
+    return out
+
+
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code (comments and blank lines left out, so
+    that a comment edit does not invalidate a capture)."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1511_01561_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1511_01561_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update("\n".join(code_lines(f.read())).encode())
     return h.hexdigest()[:16]
 
 

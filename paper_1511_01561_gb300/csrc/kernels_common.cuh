@@ -390,7 +390,10 @@ __host__ __device__ constexpr int line_group() {
 //     into the inverse mass of the DSS: the kernel writes
 //     sum_d K_d (D F_d), and the update multiplies the sum over element
 //     nodes by w_i w_j w_k / M (Minv_r) instead of 1 / M.
-
+// (3) Both forms: the nine flux components besides U (U_c u_c + p', the
+//     symmetric U_c u_d, Theta u) are formed once per global node by the
+//     update that writes the state (write_prim) and gathered as they are, not
+//     formed again at each of the global node's element nodes.
 
 // create_rhs of element e in FP64, per-node form of Eq. 5 (any element,
 // curved included), one thread per element node.  The metric terms arrive

@@ -74,6 +74,12 @@ def test_traffic_only_for_its_workload_and_sources(monkeypatch):
     assert bench.ncu_traffic(key, wl) is None
 
 
+def test_kernel_source_hash_ignores_comments_only():
+    src = 'int a = 1; // one\n/* two\n lines */ const char* s = "x//y";\n\n  // only\nb();\n'
+    assert bench.code_lines(src) == ["int a = 1;", 'const char* s = "x//y";', "b();"]
+    assert bench.code_lines(src.replace("b()", "c()")) != bench.code_lines(src)
+
+
 def test_kernel_source_hash_covers_the_kernel_files():
     csrc = os.path.join(ROOT, "paper_1511_01561_gb300", "csrc")
     for name in bench.KERNEL_SOURCES:
