@@ -1310,18 +1310,51 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
   }
 }
 
+// One block of kDssBlock global nodes of one member per iteration, as in
+// update_kernel: the member's DSS order within the block (sorted by entry
+// count), the structured box DSS on CG boxes, then the rest in natural
+// order.  Members' node ranges are padded to whole blocks in the table.
 template <int MODE, bool SHELL, typename RT>
-__global__ void __launch_bounds__(256) update_ragged(const MemberDesc* __restrict__ d,
-                                                     const RaggedGroup* __restrict__ g, int stage) {
+__global__ void __launch_bounds__(kDssBlock) update_ragged(const MemberDesc* __restrict__ d,
+                                                           const RaggedGroup* __restrict__ g, int stage) {
+  __shared__ double sums[5][kDssBlock];
+  __shared__ int s_slot;
+  __shared__ long long s_base;
   const int n = g->n;
-  const long long total = n > 0 ? g->node_prefix[n] : 0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
-    const int m = ragged_find(g->node_prefix, n, w);
-    const int slot = g->member[m];
-    const long long I = w - g->node_prefix[m];
-    if (slot >= 0 && slot < kMaxMembers && I >= 0 && I < d[slot].ua[stage].Ng)
-      update_node<MODE, SHELL, RT>(d[slot].ua[stage], I);
+  const long long total = n > 0 ? g->block_prefix[n] : 0;
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int m = ragged_find(g->block_prefix, n, b);
+      s_slot = g->member[m];
+      s_base = (b - g->block_prefix[m]) * kDssBlock;
+    }
+    __syncthreads();
+    const int slot = s_slot;
+    const long long base = s_base;
+    // (uniform across the CTA) guard against a table that disagrees with the member
+    if (slot >= 0 && slot < kMaxMembers && base >= 0 && base < d[slot].ua[stage].iend) {
+      const UpdateArgs& a = d[slot].ua[stage];
+      const int lt = a.order[base + threadIdx.x];
+      const long long IA = base + lt;
+      if (IA < a.iend) {
+        double s[5];
+        if constexpr (SHELL) {
+          dss_node<RT>(a, IA, s);
+        } else {
+          if (a.box_N) dss_box<RT>(a, IA, s);
+          else dss_node<RT>(a, IA, s);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sums[v][lt] = s[v];
+      }
+      __syncthreads();
+      const int t = threadIdx.x;
+      const long long I = base + t;
+      if (I < a.iend)
+        update_node_sums<MODE, SHELL, std::is_same<RT, float>::value>(a, I, sums[0][t], sums[1][t], sums[2][t],
+                                                                      sums[3][t], sums[4][t]);
+    }
+    __syncthreads();  // the block's slot, base and sums are rewritten in the next iteration
   }
 }
 

@@ -260,7 +260,7 @@ struct RaggedGroup {
   int n;
   int pad;
   long long elem_prefix[kMaxMembers + 1];
-  long long node_prefix[kMaxMembers + 1];
+  long long block_prefix[kMaxMembers + 1];  // blocks of kDssBlock global nodes (each member's padded to whole blocks)
   int member[kMaxMembers];
 };
 

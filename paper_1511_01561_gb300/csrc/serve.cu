@@ -241,7 +241,7 @@ void rebuild_tables(numa_sched* s) {
       s->groups.push_back(k);
       s->h_groups[g].n = 0;
       s->h_groups[g].elem_prefix[0] = 0;
-      s->h_groups[g].node_prefix[0] = 0;
+      s->h_groups[g].block_prefix[0] = 0;
     } else {
       g = it->second;
     }
@@ -249,7 +249,7 @@ void rebuild_tables(numa_sched* s) {
     const int m = G.n++;
     G.member[m] = r.slot;
     G.elem_prefix[m + 1] = G.elem_prefix[m] + r.ctx->mesh.Ne;
-    G.node_prefix[m + 1] = G.node_prefix[m] + r.ctx->mesh.Ng;
+    G.block_prefix[m + 1] = G.block_prefix[m] + (r.ctx->mesh.Ng + kDssBlock - 1) / kDssBlock;
   }
   s->tables_dirty = true;
 }

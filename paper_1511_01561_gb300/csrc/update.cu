@@ -87,16 +87,16 @@ cudaError_t launch_volume_ragged(int N, int precision, bool affine, const Member
 
 cudaError_t launch_update_ragged(int precision, bool shell, int stage, const MemberDesc* d, const RaggedGroup* g,
                                  cudaStream_t s) {
-  const int grid = 8 * sm_count();
+  const int grid = 16 * sm_count();  // persistent: blocks of kDssBlock threads loop over the groups' node blocks
   const bool f32 = precision == NUMA_FP32_MIXED;
   auto go = [&](auto mode_tag) {
     constexpr int M = decltype(mode_tag)::value;
     if (shell) {
-      if (f32) update_ragged<M, true, float><<<grid, 256, 0, s>>>(d, g, stage);
-      else update_ragged<M, true, double><<<grid, 256, 0, s>>>(d, g, stage);
+      if (f32) update_ragged<M, true, float><<<grid, kDssBlock, 0, s>>>(d, g, stage);
+      else update_ragged<M, true, double><<<grid, kDssBlock, 0, s>>>(d, g, stage);
     } else {
-      if (f32) update_ragged<M, false, float><<<grid, 256, 0, s>>>(d, g, stage);
-      else update_ragged<M, false, double><<<grid, 256, 0, s>>>(d, g, stage);
+      if (f32) update_ragged<M, false, float><<<grid, kDssBlock, 0, s>>>(d, g, stage);
+      else update_ragged<M, false, double><<<grid, kDssBlock, 0, s>>>(d, g, stage);
     }
   };
   // stage 0 of SSP-RK3 is the first stage (a = 0, b = 1)
