@@ -86,10 +86,10 @@ FP64_PEAK_SOURCE = "nominal FP64 FMA rate; measured 1.258 TFLOP/s (profiles/p0_a
 # this workload (profiles/*_bubble_32x32x32_N4.md), valid only for the kernel
 # sources they were taken on (first 16 hex digits of the sha256 of the kernel
 # sources, see kernel_source_hash).
-NCU_TRAFFIC = {"kernels_sha256_16": "255ffeb0445a8327", "workload": "bubble_32x32x32_N4",
-               "volume_fp64_affine": 223.283200e6 + 131.003648e6,
-               "volume_pairs_affine": 154.668032e6 + 122.632192e6,
-               "volume_fp32_affine": 139.263488e6 + 49.154048e6}
+NCU_TRAFFIC = {"kernels_sha256_16": "4ad10831c0debb5a", "workload": "bubble_32x32x32_N4",
+               "volume_fp64_affine": 223.360000e6 + 130.280448e6,
+               "volume_pairs_affine": 154.657536e6 + 122.701056e6,
+               "volume_fp32_affine": 139.254016e6 + 49.605376e6}
 
 KERNEL_SOURCES = ["kernels_common.cuh", "volume_fp64.cu", "volume_fp32.cu", "volume_pairs.cu", "update.cu"]
 
