@@ -642,7 +642,7 @@ int numa_bind(numa_ctx* c, void* ws, size_t bytes, void* stream) {
       // Minv_r: w_i w_j w_k of the node's first element node (its DSS list
       // is ascending), times 1/M.  Lobatto weights are symmetric, so every
       // element node of a global node of a box has that weight; a mesh
-      // where they differ keeps the general affine form.
+      // where they differ is not treated as rectilinear (volume_form).
       if (rect) {
         const long long Np = m.Np;
         Minv_r.resize((size_t)Ng);
