@@ -48,6 +48,14 @@ def test_byte_models():
     assert bench.update_bytes(Nl, Nl, 8, 2 / 3, entries=10_941_048) > cg
 
 
+def test_stage_byte_model():
+    # the scope table's figures for the 32^3 bubble: 842 MB per FP64 stage,
+    # 678 MB with FP32 metric terms
+    Nl, Ng = 4_096_000, 2_146_689
+    assert round(bench.stage_bytes_survey(Nl, Ng, 8) / 1e6) == 842
+    assert round(bench.stage_bytes_survey(Nl, Ng, 4) / 1e6) == 678
+
+
 def test_whole_job_rate():
     # node-updates per RK stage of all replicas: world * Ng * 3 stages * steps / seconds
     assert bench.whole_job_rate(1, 1000, 10, 1000.0) == pytest.approx(30_000.0)
