@@ -200,7 +200,7 @@ def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float, entries: int 
             + Ng * (4 + 8 + 1 + 40 + 40 + 40 * stage_reads_qn + 32 + prim))
 
 
-def stage_bytes_survey(Nl: int, Ng: int, fp: int) -> float:
+def stage_bytes_model(Nl: int, Ng: int, fp: int) -> float:
     """Algorithmic DRAM bytes of one whole RK stage in the byte model of the
     hot path's scope table: per element node the metric terms and Jw (10
     values of fp bytes) and l2g (4 B); per global node q^k, q^n and q^{k+1}
@@ -517,7 +517,7 @@ def run_mine(args):
                      "share_of_step": ms_vol / (ms_vol + ms_upd)},
         "kernels": {"volume_ms_avg": 1e3 * vol_avg_s, "update_ms_avg": ms_upd / nlaunch,
                     "update_hbm_frac": update_bytes(Nl, Ng, 8, 2 / 3) / (ms_upd * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
-                    "stage_hbm_frac": stage_bytes_survey(Nl, Ng, 8) / (ms * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
+                    "stage_hbm_frac": stage_bytes_model(Nl, Ng, 8) / (ms * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
                     "stage_hbm_model": "84 B per element node + 232 B per global node"},
         "clocks": ck,
         "finite": finite,
@@ -568,7 +568,7 @@ def run_mine(args):
                          "peak_source": peak_src, "avg_launch_ms": 1e3 * vol32_s},
             "update_ms_avg": upd32 / nlaunch,
             "update_hbm_frac": update_bytes(Nl, Ng, 4, 2 / 3) / (upd32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
-            "stage_hbm_frac": stage_bytes_survey(Nl, Ng, 4) / (ms32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
+            "stage_hbm_frac": stage_bytes_model(Nl, Ng, 4) / (ms32 * 1e-3 / nlaunch) / 1e9 / hbm_gbs,
             "stage_hbm_model": "44 B per element node + 232 B per global node",
         }
         if affine:

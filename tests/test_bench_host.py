@@ -52,8 +52,8 @@ def test_stage_byte_model():
     # the scope table's figures for the 32^3 bubble: 842 MB per FP64 stage,
     # 678 MB with FP32 metric terms
     Nl, Ng = 4_096_000, 2_146_689
-    assert round(bench.stage_bytes_survey(Nl, Ng, 8) / 1e6) == 842
-    assert round(bench.stage_bytes_survey(Nl, Ng, 4) / 1e6) == 678
+    assert round(bench.stage_bytes_model(Nl, Ng, 8) / 1e6) == 842
+    assert round(bench.stage_bytes_model(Nl, Ng, 4) / 1e6) == 678
 
 
 def test_whole_job_rate():
