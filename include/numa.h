@@ -252,7 +252,7 @@ int numa_set_time_scheme(numa_ctx* ctx, int scheme);
  * beside the element kernel of slab k + 1 (the element kernel is bound by
  * memory or FP64 work, the update by FP64 work and latency), ordered by
  * events so that every node is computed exactly as without slabs: results are
- * identical bit for bit.  nslabs = 0 (the default) chooses 4 slabs for
+ * identical bit for bit.  nslabs = 0 (the default) chooses 3 slabs for
  * FP32-mixed meshes of 2^18 or more global nodes (in FP64 and the pairs mode
  * both kernels compete for the same pipes and the pipeline measured no gain,
  * so it stays off there); 1 turns the pipeline off; at most 16.  Where a

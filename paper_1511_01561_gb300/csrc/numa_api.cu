@@ -376,14 +376,14 @@ __global__ void __launch_bounds__(256) weight_metric_kernel(double* met, long lo
 // lattice planes thick and planes of at least kDssBlock nodes, so that node
 // slab k (rounded down to a kDssBlock boundary) only holds nodes of element
 // slabs <= k and the element slab k reads only node slabs k and k + 1.
-// `want` slabs (0: four for FP32-mixed meshes of 2^18 or more global nodes,
+// `want` slabs (0: three for FP32-mixed meshes of 2^18 or more global nodes,
 // where the memory-bound element kernel and the FP64-bound update overlap;
 // in FP64 and the pairs mode both kernels need the FP64 pipe, or the FP32
 // pipe beside it, and the pipeline measured no gain, so none by default).
 SlabPlan plan_slabs(const numa_config& c, const HostMesh& m, int want) {
   SlabPlan P;
   if (c.mesh_kind != NUMA_MESH_BOX || c.storage != NUMA_STORAGE_CG || c.periodic[2]) return P;
-  int S = want > 0 ? want : (c.precision == NUMA_FP32_MIXED && m.Ng >= (1LL << 18) ? 4 : 1);
+  int S = want > 0 ? want : (c.precision == NUMA_FP32_MIXED && m.Ng >= (1LL << 18) ? 3 : 1);
   if (S > kMaxSlabs) S = kMaxSlabs;
   if (S > c.nez) S = c.nez;
   if (S <= 1) return P;

@@ -136,7 +136,7 @@ def test_meshes_beyond_32_bit_indices_are_refused(numa):
 
 
 @pytest.mark.parametrize("cfg,want,expect", [
-    (dict(I.box(32, 4), precision="fp32_mixed"), 0, 4),  # FP32-mixed, 2.1M nodes: four by default
+    (dict(I.box(32, 4), precision="fp32_mixed"), 0, 3),  # FP32-mixed, 2.1M nodes: three by default
     (I.box(32, 4), 0, 1),                       # FP64: none by default
     (I.box((4, 4, 8), 4), 0, 1),                # small mesh: none by default
     (I.box((4, 4, 8), 4), 4, 4),
