@@ -1,0 +1,177 @@
+"""The oracle's right-hand-side pins against planted mistakes.
+
+Each pin of tests/test_oracle_rhs.py fixes part of Eq. 1, 4 or 5 by a
+closed form, an exact balance or a convergence property.  Here the box pins
+are gathered into one set of normalised errors (value / bar: at most 1 for
+a correct oracle) and run on copies of the oracle with a plausible mistake
+planted in its C source: a transposed D or metric index, a dropped or
+misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
+weighting, an inverse mass left out, a wall condition on the wrong
+component, a wrong density in the velocity.  Every planted mistake must
+push at least one pin over its bar."""
+import numpy as np
+import pytest
+
+from paper_1511_01561_gb300 import inputs as I
+
+from .test_oracle_rhs import _gamma, _manufactured
+
+# plausible mistakes, each as textual edits of oracle/numa_oracle.c
+PLANTED = {
+    # D transposed in the eta contraction
+    "d_transposed": [("d1 += m->D[j * P + mm] * f[i + P * (mm + P * k)];",
+                      "d1 += m->D[mm * P + j] * f[i + P * (mm + P * k)];")],
+    # chain rule with the metric terms transposed (dxi_c/dx_d for dxi_d/dx_c)
+    "metric_transposed": [("s += d0 * B[0 * 3 + cc] + d1 * B[1 * 3 + cc] + d2 * B[2 * 3 + cc];",
+                           "s += d0 * B[cc * 3 + 0] + d1 * B[cc * 3 + 1] + d2 * B[cc * 3 + 2];")],
+    # p' left out of the momentum flux
+    "pressure_dropped": [("F[1 + a][cc][l] = U[a] * u[cc] + (a == cc ? pp : 0.0);",
+                          "F[1 + a][cc][l] = U[a] * u[cc];")],
+    # p' in every component of the momentum flux, not only the diagonal
+    "pressure_everywhere": [("F[1 + a][cc][l] = U[a] * u[cc] + (a == cc ? pp : 0.0);",
+                             "F[1 + a][cc][l] = U[a] * u[cc] + pp;")],
+    # Theta U (rho theta U) instead of theta U in the Theta flux
+    "theta_flux": [("F[4][cc][l] = theta * U[cc];", "F[4][cc][l] = Th * U[cc];")],
+    # buoyancy with the wrong sign
+    "buoyancy_sign": [("S[3] = -rp * c->g;", "S[3] = rp * c->g;")],
+    # residual weighted by +Jw
+    "weight_sign": [("re[v * Nl + n] = -m->Jw[n] * (div[v] - S[v]);",
+                     "re[v * Nl + n] = m->Jw[n] * (div[v] - S[v]);")],
+    # the DSS sum not divided by the mass matrix
+    "mass_missing": [("R[v * Ng + g] /= m->M[g];", "R[v * Ng + g] /= 1.0;")],
+    # the z-wall condition applied to the y momentum
+    "wall_component": [("if (b & 4) R[3 * Ng + g] = 0.0;", "if (b & 4) R[2 * Ng + g] = 0.0;")],
+    # velocity from the reference density only
+    "velocity_density": [("double u[3] = {U[0] / rho, U[1] / rho, U[2] / rho};",
+                          "double u[3] = {U[0] / m->rho0[g], U[1] / m->rho0[g], U[2] / m->rho0[g]};")],
+}
+
+
+def _pin_errors(orc, manufactured_bar):
+    """Normalised errors of the box pins: each at most 1 for a correct
+    oracle (the bars of tests/test_oracle_rhs.py)."""
+    out = {}
+    # a state at rest about its own reference: R = 0 bitwise (warped walls)
+    m = orc.Mesh(I.box(2, 4, warp=0.05))
+    out["rest"] = 0.0 if np.all(m.rhs(m.init_state("rest")) == 0.0) else np.inf
+    # uniform flow without gravity, periodic and warped: R = 0 to roundoff
+    cfg = I.box((3, 2, 2), 4, periodic=(1, 1, 1), warp=0.05, g=0.0)
+    m = orc.Mesh(cfg)
+    R = m.rhs(m.init_state("uniform", (10.0, -4.0, 2.5)))
+    out["uniform"] = np.abs(R).max() / (1e-12 * m.ref()[0].max() * 100.0 / (1000.0 / 12))
+    # linear p', U = 0 on a warped box: R_U = -grad p' exactly inside, R_rho = R_Theta = 0
+    b = np.array([3.0e-3, -2.0e-3, 5.0e-3]) * 1e3
+    cfg = I.box((2, 3, 2), 4, warp=0.06, g=0.0)
+    m = orc.Mesh(cfg)
+    xyz = m.coords()
+    _, th0, p0 = m.ref()
+    pp = b @ (xyz - xyz.mean(axis=1, keepdims=True))
+    q = np.zeros((5, m.Ng))
+    q[4] = th0 * ((1.0 + pp / p0) ** (1.0 / _gamma(cfg)) - 1.0)
+    R = m.rhs(q)
+    inner = m.wall() == 0
+    e = max(np.abs(R[1 + a][inner] + b[a]).max() for a in range(3)) / (1e-9 * np.abs(b).max())
+    out["linear_pressure"] = e if (np.all(R[0] == 0.0) and np.all(R[4] == 0.0)) else np.inf
+    # a linear density carried by a uniform velocity, g = 0, p' = 0, on a
+    # walled warped box: R_rho = -u0 . grad rho', R_U = -(u0 . grad rho') u0
+    # exactly at every node, with the wall-normal components zeroed at the
+    # walls, and R_Theta = 0 (Theta0 is uniform without gravity)
+    out["linear_advection"] = _linear_advection_error(orc)
+    # linear momentum: R_rho = -div U exactly
+    G = np.array([[0.3, -0.7, 0.2], [0.5, 0.1, -0.4], [-0.6, 0.9, 0.25]]) * 1e-2
+    m = orc.Mesh(I.box((2, 2, 3), 4, warp=0.05, g=0.0))
+    q = np.zeros((5, m.Ng))
+    q[1:4] = G @ m.coords()
+    out["linear_divergence"] = np.abs(m.rhs(q)[0] + np.trace(G)).max() / (1e-12 * 1e3 * np.abs(G).max())
+    # discrete conservation of rho' and Theta' on a walled box
+    m = orc.Mesh(I.box((3, 2, 2), 4))
+    q = I.random_perturbation(m.Ng, seed=3)
+    wall = m.wall()
+    for a in range(3):
+        q[1 + a][(wall >> a) & 1 == 1] = 0.0
+    R = m.rhs(q)
+    M = m.mass()
+    out["conservation"] = max(abs(M @ R[v]) / (1e-13 * (M @ np.abs(R[v]))) for v in (0, 4))
+    # the bubble's first RHS in closed form
+    cfg = I.box(4, 4)
+    m = orc.Mesh(cfg)
+    q = m.init_state("bubble", I.BUBBLE_PARAMS)
+    R = m.rhs(q)
+    tb = (m.wall() & 4) != 0
+    ok = np.all(R[[0, 1, 2, 4]] == 0.0) and np.all(R[3][tb] == 0.0)
+    exact = -q[0] * cfg["g"]
+    rel = np.abs(R[3][~tb] - exact[~tb]).max() / np.abs(exact[~tb]).max()
+    out["bubble_closed_form"] = rel / 1e-14 if ok else np.inf
+    # a smooth manufactured state: R close to -div F + S (one resolution)
+    cfg = I.box(4, 4, L=(1000.0, 800.0, 600.0), warp=0.04)
+    m = orc.Mesh(cfg)
+    f_state, f_rhs = _manufactured(cfg)
+    xyz = m.coords()
+    q = np.array([np.broadcast_to(f, xyz[0].shape) for f in f_state(*xyz)])
+    ex = np.array([np.broadcast_to(f, xyz[0].shape) for f in f_rhs(*xyz)])
+    R = m.rhs(q)
+    inner = m.wall() == 0
+    err = max(np.abs(R[v][inner] - ex[v][inner]).max() / np.abs(ex[v]).max() for v in range(5))
+    out["manufactured"] = err / manufactured_bar
+    return out
+
+
+def _linear_advection_error(orc):
+    a = np.array([2.0e-6, -1.0e-6, 1.5e-6])  # grad rho' (kg/m^4)
+    u0 = np.array([7.0, -3.0, 4.0])
+    cfg = I.box((2, 3, 2), 4, warp=0.06, g=0.0)
+    m = orc.Mesh(cfg)
+    xyz = m.coords()
+    rho0 = m.ref()[0]
+    rp = a @ (xyz - xyz.mean(axis=1, keepdims=True))
+    q = np.zeros((5, m.Ng))
+    q[0] = rp
+    q[1:4] = (rho0 + rp) * u0[:, None]
+    R = m.rhs(q)
+    adv = u0 @ a
+    wall = m.wall()
+    e = np.abs(R[0] + adv).max() / abs(adv)
+    for c in range(3):
+        expect = np.where((wall >> c) & 1 == 1, 0.0, -adv * u0[c])
+        e = max(e, np.abs(R[1 + c] - expect).max() / abs(adv * np.abs(u0).max()))
+    e = max(e, np.abs(R[4]).max() / abs(adv * m.ref()[1].max() / rho0.max()))
+    return e / 1e-9
+
+
+def test_linear_advection_exact(orc):
+    """A linear density carried by a uniform velocity (p' = 0, g = 0) on a
+    warped walled box: the fluxes are linear, so Eq. 5 differentiates them
+    exactly, and the wall condition zeroes exactly the wall-normal momentum
+    components."""
+    assert _linear_advection_error(orc) <= 1.0
+
+
+# The manufactured pin's bar at this one resolution: the correct oracle's
+# error at 4^3 elements, N = 4 is below 1e-2 (test_oracle_rhs.py holds the
+# convergence rate; 3e-3 at 8^3 elements).
+MANUFACTURED_BAR = 1e-2
+
+
+def test_correct_oracle_meets_every_bar(orc):
+    errs = _pin_errors(orc, MANUFACTURED_BAR)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+@pytest.fixture(scope="module")
+def variants(orc):
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            cache[name] = orc.build_variant(PLANTED[name], name)
+        return cache[name]
+
+    return get
+
+
+@pytest.mark.parametrize("mistake", sorted(PLANTED))
+def test_planted_mistake_breaks_a_pin(orc, variants, mistake):
+    with orc.using_library(variants(mistake)):
+        errs = _pin_errors(orc, MANUFACTURED_BAR)
+    broken = [k for k, v in errs.items() if not v <= 1.0]
+    assert broken, (mistake, errs)
