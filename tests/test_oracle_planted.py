@@ -1,10 +1,14 @@
 """The oracle's right-hand-side pins against planted mistakes.
 
-Each pin of tests/test_oracle_rhs.py fixes part of Eq. 1, 4 or 5 by a
-closed form, an exact balance or a convergence property.  Here the box pins
-are gathered into one set of normalised errors (value / bar: at most 1 for
-a correct oracle) and run on copies of the oracle with a plausible mistake
-planted in its C source: a transposed D or metric index, a dropped or
+The pins of tests/test_oracle_basis.py, test_oracle_mesh.py,
+test_oracle_rk.py and test_oracle_rhs.py fix the Lobatto basis, the metric
+terms, the stage loop and the right-hand side of Eqs. 1, 4 and 5 by closed
+forms, exact balances and convergence properties.  Here the box pins are
+gathered into one set of normalised errors (value / bar: at most 1 for a
+correct oracle) and run on copies of the oracle with a plausible mistake
+planted in its C source: a wrong Lobatto weight or D entry, the metric
+terms stored transposed, a weight missing from Jw, a wrong SSP-RK3
+coefficient, a transposed D or metric index in the RHS, a dropped or
 misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
 weighting, an inverse mass left out, a wall condition on the wrong
 component, a wrong density in the velocity.  Every planted mistake must
@@ -44,12 +48,96 @@ PLANTED = {
     # velocity from the reference density only
     "velocity_density": [("double u[3] = {U[0] / rho, U[1] / rho, U[2] / rho};",
                           "double u[3] = {U[0] / m->rho0[g], U[1] / m->rho0[g], U[2] / m->rho0[g]};")],
+    # Lobatto weights with |P_N| instead of P_N^2
+    "lgl_weight": [("w[i] = 2.0 / (N * (N + 1.0) * P * P);", "w[i] = 2.0 / (N * (N + 1.0) * fabs(P));")],
+    # the diagonal of D left at zero (D 1 != 0)
+    "d_diagonal": [("D[i * P + i] = -s;", "D[i * P + i] = 0.0;")],
+    # off-diagonal D with P_N(xi_i) and P_N(xi_j) exchanged
+    "d_offdiagonal": [("D[i * P + j] = PN[i] / (PN[j] * (xi[i] - xi[j]));",
+                       "D[i * P + j] = PN[j] / (PN[i] * (xi[i] - xi[j]));")],
+    # the inverse Jacobian stored transposed
+    "metric_stored_transposed": [("m->dxi[n * 9 + d * 3 + cc] = B[d][cc];", "m->dxi[n * 9 + d * 3 + cc] = B[cc][d];")],
+    # Jw missing the zeta weight
+    "jw_weight": [("m->Jw[n] = det * m->w[i] * m->w[j] * m->w[k];", "m->Jw[n] = det * m->w[i] * m->w[j];")],
+    # SSP-RK3 with the second stage's q^n coefficient 1/4 instead of 3/4
+    "rk3_coefficient": [("static const double a[3] = {0.0, 0.75, 1.0 / 3.0};",
+                         "static const double a[3] = {0.0, 0.25, 1.0 / 3.0};")],
 }
 
 
+def _basis_error(orc):
+    """The Lobatto closed forms (tests/golden/lgl_closed_forms.json),
+    quadrature exactness to degree 2N-1 and D exact on polynomials of degree
+    <= N (tests/test_oracle_basis.py), as one normalised error."""
+    import json
+    import math
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lgl_closed_forms.json")) as f:
+        cases = json.load(f)["cases"]
+    e = 0.0
+    for N, c in cases.items():
+        xi, w = orc.lgl(int(N))
+        ex_x = np.array([eval(v, {"math": math}) for v in c["nodes"]])
+        ex_w = np.array([eval(v, {"math": math}) for v in c["weights"]])
+        e = max(e, np.abs(xi - ex_x).max() / 2e-16, np.abs(w - ex_w).max() / 4e-16)
+    for N in range(1, 9):
+        xi, w = orc.lgl(N)
+        D = orc.dmatrix(N)
+        for k in range(0, 2 * N):
+            e = max(e, abs(w @ xi**k - (0.0 if k % 2 else 2.0 / (k + 1))) / 1e-14)
+        for k in range(0, N + 1):
+            exact = k * xi ** (k - 1) if k else np.zeros_like(xi)
+            e = max(e, np.abs(D @ xi**k - exact).max() / (1e-12 * max(1, N * N)))
+    return e
+
+
+def _metric_error(orc):
+    """Box metric terms and Jw in closed form, and the box volume
+    (tests/test_oracle_mesh.py)."""
+    ne, L = (2, 3, 4), (1000.0, 600.0, 800.0)
+    m = orc.Mesh(I.box(ne, 3, L=L))
+    met = m.metrics()
+    h = [L[a] / ne[a] for a in range(3)]
+    e = 0.0
+    for d in range(3):
+        for c in range(3):
+            exact = 2.0 / h[c] if c == d else 0.0
+            e = max(e, np.abs(met[3 * d + c] - exact).max() / (1e-13 * 2.0 / min(h)))
+    e = max(e, np.abs(met[9] / (h[0] * h[1] * h[2] / 8.0) - 1.0).max() / 1e-13)
+    vol = L[0] * L[1] * L[2]
+    e = max(e, abs(m.jw().sum() - vol) / (1e-12 * vol), abs(m.mass().sum() - vol) / (1e-12 * vol))
+    return e
+
+
+def _rk3_error(orc):
+    """One SSP-RK3 step of dq/dt = lambda q multiplies q by the cubic
+    Taylor polynomial of exp(z) (tests/test_oracle_rk.py)."""
+    lam = np.array([-0.3, -1.7, 0.4, -2.5])
+    z = lam * 0.8
+    q = orc.ssprk3_step(np.ones(4), 0.8, lambda x: lam * x)
+    return np.abs(q - (1 + z + z**2 / 2 + z**3 / 6)).max() / 1e-14
+
+
 def _pin_errors(orc, manufactured_bar):
-    """Normalised errors of the box pins: each at most 1 for a correct
-    oracle (the bars of tests/test_oracle_rhs.py)."""
+    """Normalised errors of the basis, metric, RK and box RHS pins: each at
+    most 1 for a correct oracle (the bars of tests/test_oracle_*.py)."""
+    out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc)}
+    try:
+        out.update(_rhs_pin_errors(orc, manufactured_bar))
+    except ValueError:  # the oracle refused to build a mesh (e.g. a Jacobian <= 0)
+        out["rhs"] = np.inf
+    return out
+
+
+def _safe(fn, orc):
+    try:
+        return fn(orc)
+    except ValueError:  # the oracle refused to build a mesh
+        return np.inf
+
+
+def _rhs_pin_errors(orc, manufactured_bar):
     out = {}
     # a state at rest about its own reference: R = 0 bitwise (warped walls)
     m = orc.Mesh(I.box(2, 4, warp=0.05))
