@@ -7,8 +7,8 @@ forms, exact balances and convergence properties.  Here the box pins are
 gathered into one set of normalised errors (value / bar: at most 1 for a
 correct oracle) and run on copies of the oracle with a plausible mistake
 planted in its C source: a wrong Lobatto weight or D entry, the metric
-terms stored transposed, a weight missing from Jw, a wrong SSP-RK3
-coefficient, a transposed D or metric index in the RHS, a dropped or
+terms stored transposed, a weight missing from Jw or M, a wrong exponent in
+the reference state or the equation of state, a wrong SSP-RK3 coefficient, a transposed D or metric index in the RHS, a dropped or
 misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
 weighting, an inverse mass left out, a wall condition on the wrong
 component, a wrong density in the velocity.  Every planted mistake must
@@ -59,6 +59,16 @@ PLANTED = {
     "metric_stored_transposed": [("m->dxi[n * 9 + d * 3 + cc] = B[d][cc];", "m->dxi[n * 9 + d * 3 + cc] = B[cc][d];")],
     # Jw missing the zeta weight
     "jw_weight": [("m->Jw[n] = det * m->w[i] * m->w[j] * m->w[k];", "m->Jw[n] = det * m->w[i] * m->w[j];")],
+    # Exner exponent R/cp for cp/R in the isentropic reference pressure
+    "exner_exponent": [("m->p0[g] = c->P00 * pow(pi0, c->cp / c->Rd);", "m->p0[g] = c->P00 * pow(pi0, c->Rd / c->cp);")],
+    # exponent R/cp for cv/cp in the isothermal reference (rho theta)_0
+    "isothermal_theta": [("m->Th0[g] = (c->P00 / c->Rd) * pow(m->p0[g] / c->P00, c->cv / c->cp);",
+                          "m->Th0[g] = (c->P00 / c->Rd) * pow(m->p0[g] / c->P00, c->Rd / c->cp);")],
+    # 1/gamma for gamma in the equation of state
+    "eos_gamma": [("return p0 * expm1(gamma * log1p(Th_pert / Th0));", "return p0 * expm1(log1p(Th_pert / Th0) / gamma);")],
+    # mass matrix from J without the quadrature weights
+    "mass_weights": [("for (long n = 0; n < m->Nl; ++n) m->M[m->l2g[n]] += m->Jw[n];",
+                      "for (long n = 0; n < m->Nl; ++n) m->M[m->l2g[n]] += m->J[n];")],
     # SSP-RK3 with the second stage's q^n coefficient 1/4 instead of 3/4
     "rk3_coefficient": [("static const double a[3] = {0.0, 0.75, 1.0 / 3.0};",
                          "static const double a[3] = {0.0, 0.25, 1.0 / 3.0};")],
@@ -110,6 +120,57 @@ def _metric_error(orc):
     return e
 
 
+def _eos_error(orc):
+    """p'(0) = 0; the log1p form against the plain difference of pressures
+    and against the binomial series of (1 + x)^gamma - 1
+    (tests/test_oracle_rhs.py)."""
+    cfg = I.box(1, 1)
+    gam = _gamma(cfg)
+    th0 = 348.0
+    p_ref = cfg["P00"] * (cfg["Rd"] * th0 / cfg["P00"]) ** gam
+    e = 0.0 if orc.pprime(0.0, th0, p_ref, gam) == 0.0 else np.inf
+    for x in (1e-4, -3e-3, 2e-2, -0.1, 0.3):
+        a = orc.pprime(x * th0, th0, p_ref, gam)
+        b = orc.pprime_naive(x * th0, th0, p_ref, cfg)
+        s, term = 0.0, 1.0
+        for k in range(1, 60):
+            term *= (gam - k + 1) / k * x
+            s += term
+        e = max(e, abs(a - b) / (1e-10 * abs(a)), abs(a - p_ref * s) / (2e-15 * abs(a)))
+    return e
+
+
+def _reference_error(orc):
+    """The box reference states in hydrostatic balance, dp0/dz = -rho0 g
+    (a polynomial fit on a fine column), and p0 = p((rho theta)_0)
+    (tests/test_oracle_rhs.py)."""
+    e = 0.0
+    for ref in ("isentropic", "isothermal"):
+        cfg = I.box((1, 1, 16), 4, L=(100.0, 100.0, 10000.0), ref=ref, T0=250.0)
+        m = orc.Mesh(cfg)
+        xyz, (rho0, th0, p0) = m.coords(), m.ref()
+        col = (np.abs(xyz[0]) < 1e-9) & (np.abs(xyz[1]) < 1e-9)
+        z, p, r = xyz[2][col], p0[col], rho0[col]
+        o = np.argsort(z)
+        z, p, r = z[o], p[o], r[o]
+        c = np.polynomial.polynomial.polyfit(z / 1e4, p / 1e5, 14)
+        dpdz = np.polynomial.polynomial.polyval(z / 1e4, np.polynomial.polynomial.polyder(c)) * 1e5 / 1e4
+        e = max(e, np.abs(dpdz / (-r * cfg["g"]) - 1.0).max() / 1e-7)
+        peos = cfg["P00"] * (cfg["Rd"] * th0 / cfg["P00"]) ** _gamma(cfg)
+        e = max(e, np.abs(peos / p0 - 1.0).max() / 1e-13)
+    return e
+
+
+def _mass_error(orc):
+    """M = sum of Jw over each node's element nodes: its total is the box
+    volume, and every node of a box with equal elements has the mass of its
+    weights times J (tests/test_oracle_mesh.py)."""
+    L = (1000.0, 600.0, 800.0)
+    m = orc.Mesh(I.box((2, 3, 4), 3, L=L))
+    vol = L[0] * L[1] * L[2]
+    return abs(m.mass().sum() - vol) / (1e-12 * vol)
+
+
 def _rk3_error(orc):
     """One SSP-RK3 step of dq/dt = lambda q multiplies q by the cubic
     Taylor polynomial of exp(z) (tests/test_oracle_rk.py)."""
@@ -122,7 +183,8 @@ def _rk3_error(orc):
 def _pin_errors(orc, manufactured_bar):
     """Normalised errors of the basis, metric, RK and box RHS pins: each at
     most 1 for a correct oracle (the bars of tests/test_oracle_*.py)."""
-    out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc)}
+    out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc),
+           "eos": _eos_error(orc), "reference": _safe(_reference_error, orc), "mass": _safe(_mass_error, orc)}
     try:
         out.update(_rhs_pin_errors(orc, manufactured_bar))
     except ValueError:  # the oracle refused to build a mesh (e.g. a Jacobian <= 0)
