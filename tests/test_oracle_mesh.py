@@ -126,3 +126,33 @@ def test_assembly_equals_brute_force(orc, cfg):
     assert np.abs(R - Ro).max() <= 1e-13 * scale.max()
     for v in range(5):
         assert np.abs(R[v] - Ro[v]).max() <= 1e-13 * scale[v, 0]
+
+
+def _equator_longitudes(orc, npanel, N):
+    """Distinct longitudes of the nodes on the equator (z = 0) of a shell
+    with an even number of columns per panel edge, sorted, in [-pi, pi)."""
+    m = orc.Mesh(I.shell(npanel, 1, N))
+    xyz = m.coords()
+    r = np.sqrt((xyz**2).sum(axis=0))
+    eq = np.abs(xyz[2]) < 1e-9 * r
+    lon = np.unique(np.round(np.arctan2(xyz[1][eq], xyz[0][eq]), 12))
+    return lon
+
+
+@pytest.mark.parametrize("npanel,N", [(2, 4), (4, 3)])
+def test_shell_is_equiangular(orc, npanel, N):
+    """Equiangular cubed sphere (Sec. 4): along a panel's central great
+    circle the element boundaries are equally spaced in angle, 90 degrees
+    per panel split into npanel elements, and inside each element the nodes
+    sit at the Lobatto points of the angle (not of the tangent)."""
+    lon = _equator_longitudes(orc, npanel, N)
+    assert lon.size == 4 * npanel * N  # every equator node, once
+    d = 0.5 * np.pi / npanel
+    xi, _ = orc.lgl(N)
+    pos = (lon + np.pi) / d  # element widths from longitude -180
+    frac = np.unique(np.round(pos % 1.0, 9) % 1.0)
+    np.testing.assert_allclose(frac, np.sort((xi[:-1] + 1.0) / 2.0), atol=1e-9)
+    corners = np.sort(lon[np.abs(pos - np.round(pos)) < 1e-9])
+    assert corners.size == 4 * npanel
+    np.testing.assert_allclose(np.diff(corners), d, atol=1e-11)
+

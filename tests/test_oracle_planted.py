@@ -7,7 +7,8 @@ forms, exact balances and convergence properties.  Here the box pins are
 gathered into one set of normalised errors (value / bar: at most 1 for a
 correct oracle) and run on copies of the oracle with a plausible mistake
 planted in its C source: a wrong Lobatto weight or D entry, the metric
-terms stored transposed, a weight missing from Jw or M, a wrong exponent in
+terms stored transposed, a weight missing from Jw or M, equidistant instead
+of equiangular cubed-sphere coordinates, a wrong exponent in
 the reference state or the equation of state, a wrong SSP-RK3 coefficient, a transposed D or metric index in the RHS, a dropped or
 misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
 weighting, an inverse mass left out, a wall condition on the wrong
@@ -69,6 +70,9 @@ PLANTED = {
     # mass matrix from J without the quadrature weights
     "mass_weights": [("for (long n = 0; n < m->Nl; ++n) m->M[m->l2g[n]] += m->Jw[n];",
                       "for (long n = 0; n < m->Nl; ++n) m->M[m->l2g[n]] += m->J[n];")],
+    # equidistant instead of equiangular panel coordinates on the cubed sphere
+    "shell_equidistant": [("double ta = tan(al), tb = tan(be);",
+                           "double ta = al * (4.0 / M_PI), tb = be * (4.0 / M_PI);")],
     # SSP-RK3 with the second stage's q^n coefficient 1/4 instead of 3/4
     "rk3_coefficient": [("static const double a[3] = {0.0, 0.75, 1.0 / 3.0};",
                          "static const double a[3] = {0.0, 0.25, 1.0 / 3.0};")],
@@ -171,6 +175,27 @@ def _mass_error(orc):
     return abs(m.mass().sum() - vol) / (1e-12 * vol)
 
 
+def _shell_error(orc):
+    """The equiangular cubed sphere (tests/test_oracle_mesh.py): element
+    boundaries equally spaced in angle along the equator, Lobatto points of
+    the angle inside each element."""
+    from .test_oracle_mesh import _equator_longitudes
+
+    npanel, N = 2, 4
+    lon = _equator_longitudes(orc, npanel, N)
+    d = 0.5 * np.pi / npanel
+    pos = (lon + np.pi) / d
+    xi, _ = orc.lgl(N)
+    frac = np.unique(np.round(pos % 1.0, 9) % 1.0)
+    if frac.size != N:
+        return np.inf
+    e = np.abs(frac - np.sort((xi[:-1] + 1.0) / 2.0)).max() / 1e-9
+    corners = np.sort(lon[np.abs(pos - np.round(pos)) < 1e-9])
+    if corners.size != 4 * npanel:
+        return np.inf
+    return max(e, np.abs(np.diff(corners) - d).max() / 1e-11)
+
+
 def _rk3_error(orc):
     """One SSP-RK3 step of dq/dt = lambda q multiplies q by the cubic
     Taylor polynomial of exp(z) (tests/test_oracle_rk.py)."""
@@ -184,7 +209,8 @@ def _pin_errors(orc, manufactured_bar):
     """Normalised errors of the basis, metric, RK and box RHS pins: each at
     most 1 for a correct oracle (the bars of tests/test_oracle_*.py)."""
     out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc),
-           "eos": _eos_error(orc), "reference": _safe(_reference_error, orc), "mass": _safe(_mass_error, orc)}
+           "eos": _eos_error(orc), "reference": _safe(_reference_error, orc), "mass": _safe(_mass_error, orc),
+           "shell": _safe(_shell_error, orc)}
     try:
         out.update(_rhs_pin_errors(orc, manufactured_bar))
     except ValueError:  # the oracle refused to build a mesh (e.g. a Jacobian <= 0)
