@@ -8,7 +8,8 @@ gathered into one set of normalised errors (value / bar: at most 1 for a
 correct oracle) and run on copies of the oracle with a plausible mistake
 planted in its C source: a wrong Lobatto weight or D entry, the metric
 terms stored transposed, a weight missing from Jw or M, equidistant instead
-of equiangular cubed-sphere coordinates, a wrong exponent in
+of equiangular cubed-sphere coordinates, a wrong jet direction or profile
+in the shell's initial state, a wrong exponent in
 the reference state or the equation of state, a wrong SSP-RK3 coefficient, a transposed D or metric index in the RHS, a dropped or
 misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
 weighting, an inverse mass left out, a wall condition on the wrong
@@ -19,7 +20,7 @@ import pytest
 
 from paper_1511_01561_gb300 import inputs as I
 
-from .test_oracle_rhs import _gamma, _manufactured
+from .test_oracle_rhs import _gamma, _jetwave_error, _manufactured
 
 # plausible mistakes, each as textual edits of oracle/numa_oracle.c
 PLANTED = {
@@ -73,6 +74,12 @@ PLANTED = {
     # equidistant instead of equiangular panel coordinates on the cubed sphere
     "shell_equidistant": [("double ta = tan(al), tb = tan(be);",
                            "double ta = al * (4.0 / M_PI), tb = be * (4.0 / M_PI);")],
+    # the jet along the radial-horizontal direction instead of eastward
+    "jet_direction": [("U[0] = -m->rho0[g] * u * sin(lam);\n      U[1] = m->rho0[g] * u * cos(lam);",
+                       "U[0] = m->rho0[g] * u * cos(lam);\n      U[1] = m->rho0[g] * u * sin(lam);")],
+    # sin(2 phi) instead of sin^2(2 phi) in the jet profile
+    "jet_profile": [("double u = Uj * s2 * s2 + amp * exp(-(d / rad) * (d / rad));",
+                     "double u = Uj * s2 + amp * exp(-(d / rad) * (d / rad));")],
     # SSP-RK3 with the second stage's q^n coefficient 1/4 instead of 3/4
     "rk3_coefficient": [("static const double a[3] = {0.0, 0.75, 1.0 / 3.0};",
                          "static const double a[3] = {0.0, 0.25, 1.0 / 3.0};")],
@@ -210,7 +217,7 @@ def _pin_errors(orc, manufactured_bar):
     most 1 for a correct oracle (the bars of tests/test_oracle_*.py)."""
     out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc),
            "eos": _eos_error(orc), "reference": _safe(_reference_error, orc), "mass": _safe(_mass_error, orc),
-           "shell": _safe(_shell_error, orc)}
+           "shell": _safe(_shell_error, orc), "jetwave": _safe(_jetwave_error, orc)}
     try:
         out.update(_rhs_pin_errors(orc, manufactured_bar))
     except ValueError:  # the oracle refused to build a mesh (e.g. a Jacobian <= 0)

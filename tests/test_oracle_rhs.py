@@ -159,6 +159,43 @@ def test_bubble_initial_state(orc):
     np.testing.assert_allclose(theta - 300.0, thp, atol=1e-11)
 
 
+def _jetwave_error(orc):
+    """The shell's stand-in state: rest perturbations rho' = Theta' = 0 and
+    a purely zonal momentum (no radial or meridional part), 35 m/s at
+    45 degrees of latitude away from the bump and none at the equator and
+    the poles away from it, a bump of 1 m/s on top at (0 E, 45 N).  Returns
+    a normalised error (at most 1 when every property holds)."""
+    Uj, amp, rad, lc, pc = I.JETWAVE_PARAMS
+    m = orc.Mesh(I.shell(3, 1, 4))
+    q = m.init_state("jetwave", I.JETWAVE_PARAMS)
+    if not (np.all(q[0] == 0.0) and np.all(q[4] == 0.0)):
+        return np.inf
+    xyz = m.coords()
+    rho0 = m.ref()[0]
+    r = np.sqrt((xyz**2).sum(axis=0))
+    lam = np.arctan2(xyz[1], xyz[0])
+    phi = np.arcsin(xyz[2] / r)
+    U = q[1:4]
+    east = np.array([-np.sin(lam), np.cos(lam), np.zeros_like(lam)])
+    if np.any(U[2] != 0.0):
+        return np.inf
+    e = np.abs((U * xyz / r).sum(axis=0)).max() / (1e-12 * np.abs(U).max())
+    u = (U * east).sum(axis=0) / rho0
+    d = np.arccos(np.clip(np.sin(pc) * np.sin(phi) + np.cos(pc) * np.cos(phi) * np.cos(lam - lc), -1, 1))
+    far = d > 5 * rad
+    at45 = np.abs(np.abs(phi) - np.pi / 4) < 1e-9
+    zero = (np.abs(phi) < 1e-9) | (np.abs(np.abs(phi) - np.pi / 2) < 1e-9)
+    if not (at45 & far).any() or not (zero & far).any():
+        return np.inf
+    e = max(e, np.abs(u[at45 & far] - Uj).max() / (1e-12 * Uj), np.abs(u[zero & far]).max() / 1e-9)
+    e = max(e, abs(u.max() - (Uj + amp)) / (0.05 * amp), max(0.0, u.max() - (Uj + amp)) / 1e-12)
+    return e
+
+
+def test_jetwave_initial_state(orc):
+    assert _jetwave_error(orc) <= 1.0
+
+
 # ------------------------------------------------------------- symmetry ----
 
 def _box_grid(m, cfg):
