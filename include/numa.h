@@ -158,7 +158,11 @@ int numa_init_state(numa_ctx* ctx, int ic_kind, const double* params, int nparam
 
 /* Copy the context's state from / to a caller buffer double[5][Ng];
  * on_device = 1 for a device pointer, 0 for host memory (pinned memory
- * makes the copy asynchronous-capable; the call waits for completion). */
+ * makes the copy asynchronous-capable; the call waits for completion).
+ * From a device pointer, numa_set_state is enqueued on the bound stream
+ * and returns without waiting; it copies the state and forms its
+ * primitive fields in one pass (the next step's first element kernel
+ * needs them). */
 int numa_set_state(numa_ctx* ctx, const double* q, int on_device);
 int numa_get_state(numa_ctx* ctx, double* q, int on_device);
 

@@ -45,6 +45,7 @@ PrimArgs prim_args(const numa_ctx* c, const double* q, void* prim) {
   a.q = q;
   a.ref = c->L.ref;
   a.prim = prim;
+  a.qcopy = nullptr;
   a.Ng = c->mesh.Ng;
   a.precision = c->cfg.precision;
   a.gamma = c->gamma;
@@ -734,9 +735,18 @@ int numa_set_state(numa_ctx* c, const double* q, int on_device) {
   c->prim_valid = false;
   c->filter_count = 0;
   c->imex_started = false;
-  cudaError_t e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  cudaError_t e;
+  if (on_device) {
+    // one pass: copy the state in and form its primitive fields (which the
+    // next step's first element kernel needs)
+    PrimArgs a = prim_args(c, q, c->L.prim);
+    a.qcopy = c->L.q;
+    e = launch_prim(a, c->stream);
+    if (e == cudaSuccess) c->prim_valid = true;
+  } else {
+    e = cudaMemcpyAsync(c->L.q, q, 5 * (size_t)c->mesh.Ng * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "numa_set_state");
   return NUMA_OK;
 }

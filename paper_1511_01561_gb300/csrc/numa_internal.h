@@ -99,6 +99,7 @@ struct PrimArgs {
   const double* q;     // state the primitives describe [5][Ng]
   const double* ref;   // [4][Ng]
   void* prim;          // output
+  double* qcopy;       // prim_kernel only: where it also copies q (nullptr: no copy)
   long long Ng;
   int precision;
   double gamma;

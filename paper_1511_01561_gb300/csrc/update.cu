@@ -1,7 +1,8 @@
 // Per-global-node kernels of the GB300 NUMA hot path (sm_103a):
 //   prim_kernel   : the primitive fields of a state, which the element
 //                   kernels build their fluxes from (FP64: the flux
-//                   components themselves; FP32 and pairs: U, u, theta, p');
+//                   components themselves; FP32 and pairs: U, u, theta, p'),
+//                   optionally copying the state in the same pass;
 //   update_kernel : deterministic direct stiffness summation over a
 //                   precomputed inverse map (fixed order, no atomics), inverse
 //                   mass matrix, sources, wall condition, the SSP-RK3 stage
@@ -20,10 +21,16 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs a) {
   const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= a.Ng) return;
   const long long Ng = a.Ng;
-  if (a.precision == NUMA_FP32_MIXED)
-    write_prim<true>(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
-  else
-    write_prim<false>(a, I, a.q[I], a.q[Ng + I], a.q[2 * Ng + I], a.q[3 * Ng + I], a.q[4 * Ng + I]);
+  const double q0 = a.q[I], q1 = a.q[Ng + I], q2 = a.q[2 * Ng + I], q3 = a.q[3 * Ng + I], q4 = a.q[4 * Ng + I];
+  if (a.qcopy) {  // (q and qcopy may be the same array: each thread rewrites its own node)
+    a.qcopy[I] = q0;
+    a.qcopy[Ng + I] = q1;
+    a.qcopy[2 * Ng + I] = q2;
+    a.qcopy[3 * Ng + I] = q3;
+    a.qcopy[4 * Ng + I] = q4;
+  }
+  if (a.precision == NUMA_FP32_MIXED) write_prim<true>(a, I, q0, q1, q2, q3, q4);
+  else write_prim<false>(a, I, q0, q1, q2, q3, q4);
 }
 
 template <int MODE, typename RT>
