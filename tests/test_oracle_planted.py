@@ -10,7 +10,8 @@ planted in its C source: a wrong Lobatto weight or D entry, the metric
 terms stored transposed, a weight missing from Jw or M, equidistant instead
 of equiangular cubed-sphere coordinates, a wrong jet direction or profile
 in the shell's initial state, a wrong exponent in
-the reference state or the equation of state, a wrong SSP-RK3 coefficient, a transposed D or metric index in the RHS, a dropped or
+the reference state or the equation of state, a wrong SSP-RK3 or
+low-storage coefficient, the low-storage stages in the wrong order, a transposed D or metric index in the RHS, a dropped or
 misplaced pressure term, a wrong flux, a sign error in the buoyancy or the
 weighting, an inverse mass left out, a wall condition on the wrong
 component, a wrong density in the velocity.  Every planted mistake must
@@ -80,6 +81,11 @@ PLANTED = {
     # sin(2 phi) instead of sin^2(2 phi) in the jet profile
     "jet_profile": [("double u = Uj * s2 * s2 + amp * exp(-(d / rad) * (d / rad));",
                      "double u = Uj * s2 + amp * exp(-(d / rad) * (d / rad));")],
+    # a digit dropped from one five-stage low-storage coefficient
+    "ls54_coefficient": [("5161836677717.0 / 13612068292357.0", "516183667771.0 / 13612068292357.0")],
+    # the low-storage update reading dq before it is refreshed
+    "ls54_stage_order": [("      dq[t] = kLsA[s] * dq[t] + dt * r[t];\n      q[t] += kLsB[s] * dq[t];",
+                          "      q[t] += kLsB[s] * dq[t];\n      dq[t] = kLsA[s] * dq[t] + dt * r[t];")],
     # SSP-RK3 with the second stage's q^n coefficient 1/4 instead of 3/4
     "rk3_coefficient": [("static const double a[3] = {0.0, 0.75, 1.0 / 3.0};",
                          "static const double a[3] = {0.0, 0.25, 1.0 / 3.0};")],
@@ -203,6 +209,21 @@ def _shell_error(orc):
     return max(e, np.abs(np.diff(corners) - d).max() / 1e-11)
 
 
+def _ls54_error(orc):
+    """One five-stage low-storage step on a linear system agrees with
+    exp(Z) through Z^4 (the rest O(dt^5): halving dt divides the
+    difference by about 32; tests/test_oracle_rk.py)."""
+    A = np.array([[-0.3, 1.2, 0.0], [-1.1, -0.2, 0.4], [0.1, 0.0, -0.9]])
+    q0 = np.array([1.0, -2.0, 0.5])
+    res = []
+    for dt in (0.2, 0.1):
+        Z = A * dt
+        taylor4 = np.eye(3) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+        res.append(np.abs(orc.lsrk54_step(q0, dt, lambda q: A @ q) - taylor4 @ q0).max())
+    ratio = res[0] / res[1]
+    return 0.0 if 28.0 < ratio < 36.0 else np.inf
+
+
 def _rk3_error(orc):
     """One SSP-RK3 step of dq/dt = lambda q multiplies q by the cubic
     Taylor polynomial of exp(z) (tests/test_oracle_rk.py)."""
@@ -216,6 +237,7 @@ def _pin_errors(orc, manufactured_bar):
     """Normalised errors of the basis, metric, RK and box RHS pins: each at
     most 1 for a correct oracle (the bars of tests/test_oracle_*.py)."""
     out = {"basis": _basis_error(orc), "metric": _safe(_metric_error, orc), "rk3": _rk3_error(orc),
+           "ls54": _ls54_error(orc),
            "eos": _eos_error(orc), "reference": _safe(_reference_error, orc), "mass": _safe(_mass_error, orc),
            "shell": _safe(_shell_error, orc), "jetwave": _safe(_jetwave_error, orc)}
     try:
