@@ -380,3 +380,102 @@ def test_planted_mistake_breaks_a_pin(orc, variants, mistake):
         errs = _pin_errors(orc, MANUFACTURED_BAR)
     broken = [k for k, v in errs.items() if not v <= 1.0]
     assert broken, (mistake, errs)
+
+
+# ------------------------------------------------------------- the filter ----
+# The pins of tests/test_oracle_filter.py (Sec. 2.3) as normalised errors, run
+# on copies of the oracle with a mistake planted in the filter's C code.
+
+FILTER_PLANTED = {
+    # F transposed in the xi sweep of the tensor product
+    "filter_transposed": [("for (int mm = 0; mm < P; ++mm) a += F[i * P + mm] * u[mm + P * (j + P * k)];",
+                           "for (int mm = 0; mm < P; ++mm) a += F[mm * P + i] * u[mm + P * (j + P * k)];")],
+    # the factor 2 dropped from the erfc argument
+    "filter_erfc_factor": [("sg = 0.5 * erfc(2.0 * sqrt(p) * chi * om);", "sg = 0.5 * erfc(sqrt(p) * chi * om);")],
+    # the DSS of the filtered values without the Jw weights
+    "filter_unweighted_dss": [("acc[v * Ng + m->l2g[e * NP + l]] += m->Jw[e * NP + l] * t[l];",
+                               "acc[v * Ng + m->l2g[e * NP + l]] += t[l];")],
+    # the z walls' normal momentum filtered like the rest
+    "filter_wall": [("if (b & 4) out[3] = q[3 * Ng + g];", "")],
+    # the strength applied to the weight instead of to its damping
+    "filter_strength": [("sigma[k] = 1.0 - mu * (1.0 - sg);", "sigma[k] = mu * sg;")],
+    # the damped modes counted from s - 1
+    "filter_first_mode": [("double theta = (s >= N) ? 1.0 : (double)(k - s) / (double)(N - s);",
+                           "double theta = (s >= N) ? 1.0 : (double)(k - s + 1) / (double)(N - s);")],
+}
+
+P_ORDER = 12.0
+
+
+def _filter_pin_errors(orc):
+    from numpy.polynomial import legendre as L
+
+    out = {}
+    # closed forms of the weights: kept modes 1, theta = 1/2 gives 1/2, the
+    # top mode 0, the erfc-log symmetry, the strength blend
+    s = orc.filter_weights(4, 2, P_ORDER)
+    s6 = orc.filter_weights(6, 2, P_ORDER)
+    ok = (np.array_equal(s[:3], [1.0, 1.0, 1.0]) and s[3] == 0.5 and s[4] == 0.0 and s6[4] == 0.5
+          and abs(s6[3] + s6[5] - 1.0) < 1e-15
+          and np.allclose(orc.filter_weights(6, 2, P_ORDER, 0.3), 1.0 - 0.3 * (1.0 - s6), atol=1e-15, rtol=0))
+    # Vandeven's filter 1 - I_theta(p, p) at p = 12, N = 8, s = 0, within 0.02
+    # (its values from the regularised incomplete beta function, scipy)
+    betainc = pytest.importorskip("scipy.special").betainc
+    sig = orc.filter_weights(8, 0, P_ORDER)
+    vand = 1.0 - betainc(P_ORDER, P_ORDER, np.arange(9) / 8.0)
+    out["weights"] = 0.0 if ok and np.abs(sig - vand).max() < 0.02 else np.inf
+    # F P_k = sigma_k P_k at the Lobatto points
+    e = 0.0
+    for N, sm in ((4, 2), (6, 3)):
+        xi, _ = orc.lgl(N)
+        F = orc.filter_matrix(N, sm, P_ORDER)
+        sg = orc.filter_weights(N, sm, P_ORDER)
+        for k in range(N + 1):
+            pk = L.legval(xi, np.eye(N + 1)[k])
+            e = max(e, np.abs(F @ pk - sg[k] * pk).max() / 5e-14)
+    out["eigenvectors"] = e
+    # one walled element: (F x F x F) q exactly
+    N = 4
+    m = orc.Mesh(I.box(1, N, L=(800.0, 900.0, 1000.0)))
+    F = orc.filter_matrix(N, 2, P_ORDER)
+    rng = np.random.default_rng(3)
+    q = rng.standard_normal((5, m.Ng))
+    res = m.filter(q, 2, P_ORDER)
+    xyz = m.coords()
+    K = np.kron(F, np.kron(F, F))
+    order = np.lexsort((xyz[0], xyz[1], xyz[2]))
+    ref = np.empty(m.Ng)
+    ref[order] = K @ q[0][order]
+    out["tensor_product"] = np.abs(res[0] - ref).max() / (1e-13 * np.abs(q[0]).max())
+    # conservation of rho' and Theta' on a walled affine box, and the walls'
+    # normal momentum kept
+    m = orc.Mesh(I.box((3, 2, 2), 4))
+    q = rng.standard_normal((5, m.Ng))
+    M = m.mass()
+    res = m.filter(q, 2, P_ORDER)
+    e = max(abs(M @ res[v] - M @ q[v]) / (1e-12 * (M @ np.abs(q[v]))) for v in (0, 4))
+    wall = m.wall()
+    for a in range(3):
+        w = (wall & (1 << a)) != 0
+        if not np.array_equal(res[1 + a][w], q[1 + a][w]):
+            e = np.inf
+    out["conservation_walls"] = e
+    # fields of degree < s per coordinate are kept (affine elements)
+    m = orc.Mesh(I.box((3, 2, 2), 5, L=(900.0, 600.0, 700.0)))
+    x, y, z = m.coords() / 1000.0
+    f = 1.0 + x - 2 * y * y + 0.5 * x * z + x * x * y * z * z
+    qf = np.stack([f, 2 * f, -f, 0.5 * f, 3 * f])
+    out["low_degree"] = np.abs(m.filter(qf, 3, P_ORDER) - qf).max() / (1e-13 * np.abs(qf).max())
+    return out
+
+
+def test_correct_filter_meets_every_bar(orc):
+    errs = _filter_pin_errors(orc)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("mistake", sorted(FILTER_PLANTED))
+def test_planted_filter_mistake_breaks_a_pin(orc, mistake):
+    with orc.using_library(orc.build_variant(FILTER_PLANTED[mistake], mistake)):
+        errs = _filter_pin_errors(orc)
+    assert [k for k, v in errs.items() if not v <= 1.0], (mistake, errs)
