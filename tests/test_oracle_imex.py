@@ -30,9 +30,15 @@ def test_column_derivative_exact_on_polynomials(imex, N):
         exact = j * z ** (j - 1) if j else np.zeros_like(z)
         scale = max(1.0, np.abs(exact).max())
         assert np.abs(Dz @ z**j - exact).max() <= 1e-11 * scale
-    if N >= 2:  # a kink at an element boundary is not differentiated exactly
-        f = np.abs(z - 400.0)
-        assert np.abs(Dz @ f - np.sign(z - 400.0)).max() > 1e-3
+    # a kink at the node z = 400 shared by elements of heights 270 (below) and
+    # 60 (above): the one-sided derivatives -1 and +1 meet at that node,
+    # averaged by the mass each element gives it (w_N h_below / 2 and
+    # w_0 h_above / 2, w_0 = w_N), i.e. (60 - 270) / (60 + 270); every other
+    # node sees a linear function
+    f = np.abs(z - 400.0)
+    expect = np.sign(z - 400.0)
+    expect[z == 400.0] = (60.0 - 270.0) / (60.0 + 270.0)
+    assert np.abs(Dz @ f - expect).max() <= 1e-11
 
 
 def _column_perturbation(m, zwall_W_zero=True):
@@ -71,6 +77,33 @@ def test_L_is_the_linearised_rhs(orc, imex, cfg):
     assert errs[1].max() <= 1e-9, errs
     assert np.all(errs[1] <= 0.02 * errs[0] + 1e-14), errs  # eps^2 convergence
     assert np.abs(Lq[3][(m.wall() & 4) != 0]).max() == 0.0
+
+
+def _solve_residual(orc, imex, cfg, tau, seed=5):
+    """x = solve(tau, b) for a random b of atmospheric scale; the largest
+    residual |x - tau L x - b| over the five variables, relative to
+    |b| + tau |L x|.  L is pinned above as the linearised right-hand side,
+    so this holds the column solve (its dense blocks and the momentum
+    correction along r_hat) to inverting I - tau L."""
+    m = orc.Mesh(cfg)
+    cols = imex.VerticalColumns(m)
+    rho0, Th0, _ = m.ref()
+    b = np.random.default_rng(seed).standard_normal((5, m.Ng))
+    b[0] *= 1e-3 * rho0
+    b[4] *= 1e-3 * Th0
+    x = cols.solve(tau, b)
+    Lx = cols.apply(x)
+    res = x - tau * Lx - b
+    return max(np.abs(res[v]).max() / (np.abs(b[v]).max() + tau * np.abs(Lx[v]).max()) for v in range(5))
+
+
+SOLVE_BAR = 1e-12
+
+
+@pytest.mark.parametrize("where,tau", [("box", 0.4), ("box", 5.0), ("shell", 10.0), ("shell", 20.0)])
+def test_solve_inverts_I_minus_tau_L(orc, imex, where, tau):
+    cfg = THIN if where == "box" else _thin_shell(3)
+    assert _solve_residual(orc, imex, cfg, tau) <= SOLVE_BAR
 
 
 def _linear_problem(n=4, seed=1, stiff=3.0):

@@ -479,3 +479,206 @@ def test_planted_filter_mistake_breaks_a_pin(orc, mistake):
     with orc.using_library(orc.build_variant(FILTER_PLANTED[mistake], mistake)):
         errs = _filter_pin_errors(orc)
     assert [k for k, v in errs.items() if not v <= 1.0], (mistake, errs)
+
+
+# ------------------------------------------------------------- 1D-IMEX ----
+# The pins of tests/test_oracle_imex.py (Sec. 2.2) as normalised errors, run on
+# copies of the Python IMEX oracle (oracle/imex.py) with a mistake planted in
+# its source: each copy is the module's text with one edit, executed as a
+# fresh module of the oracle package.
+
+IMEX_PLANTED = {
+    # buoyancy with the wrong sign, in L and in its column blocks alike
+    "gravity_sign": [("- self.glev * rho)", "+ self.glev * rho)"),
+                     ("Lc[nz:2 * nz, :nz] = -np.diag(self.glev) * keep",
+                      "Lc[nz:2 * nz, :nz] = np.diag(self.glev) * keep")],
+    # the sound speed without gamma (p' linearised as p0 Theta' / Theta0)
+    "gamma_dropped": [("self.c2 = gamma * p0 / Th0", "self.c2 = p0 / Th0")],
+    # Theta0 for the potential temperature Theta0 / rho0
+    "theta0_is_Theta0": [("self.theta0 = Th0 / rho0", "self.theta0 = Th0")],
+    # theta0 taken out of the derivative of theta0 W (exact only where theta0
+    # is constant, as in an isentropic reference state)
+    "theta0_outside_derivative": [("out[4, c] = -(Dz @ tw + self.r2 * tw)",
+                                   "out[4, c] = -(self.theta0[c] * (Dz @ W) + self.r2 * tw)")],
+    # the vertical momentum rows of L kept at the bottom and top walls
+    "wall_rows_kept": [("LW = np.where(self.zwall[c], 0.0, -Dz @ (self.c2[c] * Th) - self.glev * rho)",
+                        "LW = -Dz @ (self.c2[c] * Th) - self.glev * rho")],
+    # the column derivative assembled without the element Jacobians: an
+    # unweighted mean of the one-sided derivatives at shared nodes (exact on
+    # polynomials, wrong at a kink between elements of unequal height)
+    "derivative_unweighted": [("A[np.ix_(idx, idx)] += (w * jac)[:, None] * (D / jac)",
+                               "A[np.ix_(idx, idx)] += w[:, None] * (D / jac)"),
+                              ("mass[idx] += w * jac", "mass[idx] += w")],
+    # c2 taken out of the derivative in the column blocks (not in L itself)
+    "block_c2_outside": [("Lc[nz:2 * nz, 2 * nz:] = -(Dz * self.c2[nodes][None, :]) * keep",
+                          "Lc[nz:2 * nz, 2 * nz:] = -(self.c2[nodes][:, None] * Dz) * keep")],
+    # the momentum left as b_U, without the implicit change of its radial part
+    "momentum_uncorrected": [("x[1:4, nodes] = b[1:4, nodes] + (sol[nz:2 * nz] - bW[nodes]) * self.nhat[:, nodes]",
+                              "x[1:4, nodes] = b[1:4, nodes]")],
+    # the start step over dt instead of dt / 2 (backward Euler for L)
+    "start_full_step": [("b = q0 + dt * R(q0) - 0.5 * dt * Lop(q0)\n    return solve(0.5 * dt, b)",
+                         "b = q0 + dt * R(q0) - dt * Lop(q0)\n    return solve(dt, b)")],
+    # the explicit L term removed from q^n alone, not from 2 q^n - q^{n-1}
+    "correction_from_q_n": [("b = q_star - dt * Lop(2.0 * q_cur - q_prev)", "b = q_star - dt * Lop(q_cur)")],
+    # the Robert-Asselin filter with the wrong sign
+    "asselin_sign": [("return q_next, q_cur + nu * (q_prev - 2.0 * q_cur + q_next)",
+                      "return q_next, q_cur - nu * (q_prev - 2.0 * q_cur + q_next)")],
+    # no 2 W / r term in the divergence along a radial column
+    "spherical_divergence_dropped": [("self.r2 = 2.0 / r", "self.r2 = np.zeros_like(r)")],
+    # constant gravity g0 along a radial column instead of g0 (a / r)^2
+    "flat_gravity": [("self.glev = float(cfg[\"g\"]) * (a / r) ** 2",
+                      "self.glev = np.full_like(r, float(cfg[\"g\"]))")],
+}
+
+
+def _imex_variant(edits, tag):
+    """oracle/imex.py with textual edits [(old, new), ...], each old snippet
+    occurring exactly once, run as a new module of the oracle package (its
+    relative import of the C oracle's binding resolves as in the original)."""
+    import types
+
+    from oracle import imex
+
+    with open(imex.__file__) as f:
+        src = f.read()
+    for old, new in edits:
+        n = src.count(old)
+        if n != 1:
+            raise ValueError(f"edit target occurs {n} times: {old!r}")
+        src = src.replace(old, new)
+    mod = types.ModuleType(f"oracle.imex_planted_{tag}")
+    mod.__package__ = "oracle"
+    exec(compile(src, f"<oracle/imex.py, {tag}>", "exec"), mod.__dict__)
+    return mod
+
+
+IMEX_ISOTHERMAL = I.box((2, 2, 3), 4, L=(3000.0, 3000.0, 1500.0), periodic=(1, 1, 0), ref="isothermal", T0=250.0)
+
+
+def _imex_pin_errors(orc, mod, box_reference):
+    from .test_oracle_imex import (SOLVE_BAR, THIN, THIN_BUBBLE, _column_perturbation, _linear_problem,
+                                   _solve_residual, _thin_shell)
+
+    def in_range(r, lo, hi):
+        return max(lo / r, r / hi) if r > 0 else np.inf
+
+    out = {}
+    # the column derivative is exact on polynomials of degree <= N, on
+    # elements of unequal height
+    edges = np.array([0.0, 130.0, 400.0, 460.0, 1000.0])
+    e = 0.0
+    for N in (2, 4):
+        xi, _ = orc.lgl(N)
+        z = np.concatenate([a + 0.5 * (1 + xi[:-1]) * (b - a) for a, b in zip(edges[:-1], edges[1:])]
+                           + [edges[-1:]])
+        Dz = mod.cg_derivative_1d(z, N)
+        for j in range(N + 1):
+            exact = j * z ** (j - 1) if j else np.zeros_like(z)
+            e = max(e, np.abs(Dz @ z**j - exact).max() / (1e-11 * max(1.0, np.abs(exact).max())))
+        # at a kink on a shared node the one-sided derivatives are averaged by
+        # the mass each element gives the node
+        expect = np.sign(z - 400.0)
+        expect[z == 400.0] = (60.0 - 270.0) / (60.0 + 270.0)
+        e = max(e, np.abs(Dz @ np.abs(z - 400.0) - expect).max() / 1e-11)
+    out["derivative"] = e
+    # L is the central-difference linearisation of the full right-hand side
+    # for height-only perturbations (isentropic and isothermal references),
+    # with the W rows zero at the walls
+    e = 0.0
+    for cfg in (THIN, IMEX_ISOTHERMAL):
+        m = orc.Mesh(cfg)
+        cols = mod.VerticalColumns(m)
+        dq = _column_perturbation(m)
+        Lq = cols.apply(dq)
+        fd = (m.rhs(1e-3 * dq) - m.rhs(-1e-3 * dq)) / 2e-3
+        e = max([e] + [np.abs(fd[v] - Lq[v]).max() / (1e-9 * np.abs(Lq[v]).max()) for v in (0, 3, 4)])
+        if np.abs(Lq[3][(m.wall() & 4) != 0]).max() != 0.0:
+            e = np.inf
+    out["L_box"] = e
+    # the same on a thin shell, for radial perturbations W(r) r_hat
+    cfg = _thin_shell(3)
+    m = orc.Mesh(cfg)
+    cols = mod.VerticalColumns(m)
+    xyz = m.coords()
+    h = (np.sqrt((xyz**2).sum(0)) - cfg["r_inner"]) / 12e3
+    rho0, Th0, _ = m.ref()
+    W = rho0 * np.sin(np.pi * h) * np.cos(1.3 * h)
+    W[(m.wall() & 8) != 0] = 0.0
+    dq = np.zeros((5, m.Ng))
+    dq[0] = 1e-3 * rho0 * np.sin(2.1 * h + 0.3)
+    dq[1:4] = cols.nhat * W
+    dq[4] = 1e-3 * Th0 * np.cos(3.0 * h)
+    Lq = cols.apply(dq)
+    fd = (m.rhs(1e-3 * dq) - m.rhs(-1e-3 * dq)) / 2e-3
+    out["L_shell"] = max(np.abs(a - b).max() / (1e-9 * np.abs(b).max())
+                         for a, b in ((fd[0], Lq[0]), (cols.radial(fd), cols.radial(Lq)), (fd[4], Lq[4])))
+    # the column solve inverts I - tau L
+    out["solve"] = max(_solve_residual(orc, mod, THIN, 5.0), _solve_residual(orc, mod, _thin_shell(3), 20.0)) / SOLVE_BAR
+    # R = L = B: the start step is the Cayley map of dt / 2 (forward Euler
+    # and the trapezoidal rule over dt for q^0 -> q^1), a step the Cayley map
+    # of dt from the filtered q^{n-1}
+    _, B, q0 = _linear_problem()
+    n = len(q0)
+    R = Lop = lambda q: B @ q
+    solve = lambda tau, b: np.linalg.solve(np.eye(n) - tau * B, b)
+    cay = lambda hh: np.linalg.solve(np.eye(n) - hh * B, np.eye(n) + hh * B)
+    dt = 0.37
+    q1 = mod.lf_imex_start(R, Lop, solve, q0, dt)
+    q2, _ = mod.lf_imex_step(R, Lop, solve, q0 + 0.1, q1, dt, 0.0)
+    out["cayley"] = max(np.abs(q1 - cay(dt / 2) @ q0).max(), np.abs(q2 - cay(dt) @ (q0 + 0.1)).max()) / 1e-13
+    # second order on a linear system with an explicit part
+    from scipy.linalg import expm
+
+    A, B, q0 = _linear_problem()
+    R = lambda q: (A + B) @ q
+    Lop = lambda q: B @ q
+    ex = expm((A + B) * 2.0) @ q0
+    errs = [np.abs(mod.lf_imex_run(R, Lop, solve, q0, dt, int(round(2.0 / dt)), 0.0)[0] - ex).max()
+            for dt in (0.01, 0.005, 0.0025)]
+    out["second_order"] = max(in_range(a / b, 3.6, 4.4) for a, b in zip(errs, errs[1:]))
+    # Asselin's recurrence on the oscillation equation (nu = 0.2)
+    nu, w, dt = 0.2, 1.0, 0.3
+    z = 1j * w * dt
+    mu = np.linalg.eigvals(np.array([[2 * z, 1.0], [1 - 2 * nu + 2 * nu * z, 2 * nu]]))
+    phys = mu[np.argmax(np.abs(mu))]
+    R = lambda q: 1j * w * q
+    qa, _ = mod.lf_imex_run(R, lambda q: 0.0 * q, lambda tau, b: b, np.array([1.0 + 0.0j]), dt, 400, nu)
+    qb, _ = mod.lf_imex_run(R, lambda q: 0.0 * q, lambda tau, b: b, np.array([1.0 + 0.0j]), dt, 401, nu)
+    out["asselin"] = abs(qb[0] / qa[0] - phys) / 1e-9
+    # past the explicit limit on the thin box the run stays near a fine
+    # explicit run
+    m = orc.Mesh(THIN)
+    qi, _ = mod.run_imex(m, m.init_state("bubble", THIN_BUBBLE), 0.4, 20, 0.05)
+    if not np.isfinite(qi).all():
+        out["stable"] = np.inf
+    else:
+        out["stable"] = max(np.abs(qi[3] - box_reference[3]).max() / (0.1 * np.abs(box_reference[3]).max()),
+                            np.abs(qi[0] - box_reference[0]).max() / (0.05 * np.abs(box_reference[0]).max()))
+    return out
+
+
+@pytest.fixture(scope="module")
+def imex_box_reference(orc):
+    """A fine explicit run of the bubble on the thin box to t = 8 s."""
+    from .test_oracle_imex import THIN, THIN_BUBBLE
+
+    m = orc.Mesh(THIN)
+    return m.run(m.init_state("bubble", THIN_BUBBLE), 0.02, 400)
+
+
+def test_correct_imex_meets_every_bar(orc, imex_box_reference):
+    from oracle import imex
+
+    errs = _imex_pin_errors(orc, imex, imex_box_reference)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+def test_imex_variant_without_edits_is_the_oracle(orc, imex_box_reference):
+    errs = _imex_pin_errors(orc, _imex_variant([], "none"), imex_box_reference)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("mistake", sorted(IMEX_PLANTED))
+def test_planted_imex_mistake_breaks_a_pin(orc, imex_box_reference, mistake):
+    errs = _imex_pin_errors(orc, _imex_variant(IMEX_PLANTED[mistake], mistake), imex_box_reference)
+    assert [k for k, v in errs.items() if not v <= 1.0], (mistake, errs)
