@@ -56,6 +56,37 @@ def test_stage_byte_model():
     assert round(bench.stage_bytes_model(Nl, Ng, 4) / 1e6) == 678
 
 
+def test_reading_of_the_papers_performance_model():
+    """Tables 1 and 2 (Sec. 6) read as totals per BG/Q node over the whole
+    bubble run: their intensity and optimal-runtime rows follow from the flop
+    and traffic rows under that reading, and per grid point and right-hand
+    side the CG column is 905 flops and 641 + 199 B (1305 B with scattered
+    access).  The scope table's byte model of one stage is less than half of
+    that at the paper's p = 3."""
+    import json
+
+    with open(os.path.join(ROOT, "tests", "golden", "paper_performance_model.json")) as f:
+        g = json.load(f)
+    w = g["workload"]
+    assert w["rhs_evaluations"] == 5 * w["time_steps"]
+    per_point_rhs = w["grid_points"] / w["nodes"] * w["rhs_evaluations"]
+    for table in ("table1", "table2"):
+        for col in g[table].values():
+            traffic = col["read_gb"] + col["write_gb"]
+            assert abs(col["gflops"] / traffic - col["intensity"]) <= 0.005
+            assert abs(traffic / w["stream_gbs"] - col["runtime_s"]) <= 0.005
+    cg, cg_scattered = g["table1"]["CG"], g["table2"]["CG"]
+    assert round(cg["gflops"] * 1e9 / per_point_rhs) == 905
+    assert [round(cg[k] * 1e9 / per_point_rhs) for k in ("read_gb", "write_gb")] == [641, 199]
+    assert round((cg_scattered["read_gb"] + cg_scattered["write_gb"]) * 1e9 / per_point_rhs) == 1305
+    # 32^3 elements at N = 3: 425 B per global node and stage in FP64
+    N, ne = 3, 32
+    Nl, Ng = ne**3 * (N + 1) ** 3, (ne * N + 1) ** 3
+    ours = bench.stage_bytes_model(Nl, Ng, 8) / Ng
+    assert round(ours) == 425
+    assert ours < 0.55 * (cg["read_gb"] + cg["write_gb"]) * 1e9 / per_point_rhs
+
+
 def test_whole_job_rate():
     # node-updates per RK stage of all replicas: world * Ng * 3 stages * steps / seconds
     assert bench.whole_job_rate(1, 1000, 10, 1000.0) == pytest.approx(30_000.0)
