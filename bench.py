@@ -202,11 +202,11 @@ def update_bytes(Nl: int, Ng: int, fp: int, stage_reads_qn: float, entries: int 
 
 
 def stage_bytes_model(Nl: int, Ng: int, fp: int) -> float:
-    """Algorithmic DRAM bytes of one whole RK stage in the byte model of the
-    hot path's scope table: per element node the metric terms and Jw (10
-    values of fp bytes) and l2g (4 B); per global node q^k, q^n and q^{k+1}
-    (40 B each), the reference state (24 B), M^-1 (8 B) and the residual
-    round trip of the global DSS (80 B)."""
+    """Algorithmic DRAM bytes of one whole RK stage, counted the way the
+    paper's performance model counts (Sec. 6): per element node the metric
+    terms and Jw (10 values of fp bytes) and l2g (4 B); per global node q^k,
+    q^n and q^{k+1} (40 B each), the reference state (24 B), M^-1 (8 B) and
+    the residual round trip of the global DSS (80 B)."""
     return Nl * (10 * fp + 4) + Ng * 232
 
 

@@ -49,7 +49,7 @@ def test_byte_models():
 
 
 def test_stage_byte_model():
-    # the scope table's figures for the 32^3 bubble: 842 MB per FP64 stage,
+    # the stage byte model on the 32^3 bubble: 842 MB per FP64 stage,
     # 678 MB with FP32 metric terms
     Nl, Ng = 4_096_000, 2_146_689
     assert round(bench.stage_bytes_model(Nl, Ng, 8) / 1e6) == 842
@@ -61,7 +61,7 @@ def test_reading_of_the_papers_performance_model():
     bubble run: their intensity and optimal-runtime rows follow from the flop
     and traffic rows under that reading, and per grid point and right-hand
     side the CG column is 905 flops and 641 + 199 B (1305 B with scattered
-    access).  The scope table's byte model of one stage is less than half of
+    access).  The stage byte model of this library is less than half of
     that at the paper's p = 3."""
     import json
 
